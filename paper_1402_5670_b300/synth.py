@@ -1,0 +1,107 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+The paper denoises 512x512 grayscale natural images with additive Gaussian noise
+(Sec. 5.3) and 192x192x192 grayscale videos (Sec. 5.6). Those images and videos are
+not available here; these generators stand in for them with cartoon-like content of
+the same shape and value range: piecewise-smooth images (ellipses with smooth
+intensity ramps and curved edges, values in [0, 255]) and volumes of moving
+ellipses (one frame per index of axis 0).
+
+This module holds no shearlet arithmetic. It is shared by the tests, the benchmark
+and the oracle checks so that every side sees the same inputs.
+"""
+from __future__ import annotations
+
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.PCG64(int(seed)))
+
+
+def piecewise_smooth_image(shape: Sequence[int], seed: int) -> np.ndarray:
+    """A cartoon-like image in [0, 255] (float32): a smooth background ramp, 12
+    rotated ellipses drawn on top of each other, each with its own linear intensity
+    ramp, and 3 curved edges y > a sin(w x + phi) + b that add a step."""
+    n0, n1 = int(shape[0]), int(shape[1])
+    r = _rng(seed)
+    y, x = np.meshgrid(np.arange(n0, dtype=np.float64), np.arange(n1, dtype=np.float64),
+                       indexing="ij")
+    m = float(max(n0, n1))
+    img = (r.uniform(60, 140) + r.uniform(-40, 40) * (y / n0 - 0.5)
+           + r.uniform(-40, 40) * (x / n1 - 0.5))
+    for _ in range(12):
+        cy, cx = r.uniform(0, n0), r.uniform(0, n1)
+        ay, ax = r.uniform(m / 16, m / 3), r.uniform(m / 16, m / 3)
+        th = r.uniform(0, np.pi)
+        c, s = np.cos(th), np.sin(th)
+        u = ((y - cy) * c + (x - cx) * s) / ay
+        v = (-(y - cy) * s + (x - cx) * c) / ax
+        inside = (u * u + v * v) <= 1.0
+        gy, gx = r.uniform(-1, 1, size=2)
+        val = r.uniform(20, 235) + 30.0 * (gy * (y - cy) + gx * (x - cx)) / m
+        img = np.where(inside, val, img)
+    for _ in range(3):
+        a = r.uniform(0.02, 0.15) * n0
+        w = r.uniform(1.0, 6.0) * 2 * np.pi / n1
+        phi = r.uniform(0, 2 * np.pi)
+        b = r.uniform(0.1, 0.9) * n0
+        step = r.uniform(-40, 40)
+        img = np.where(y > a * np.sin(w * x + phi) + b, img + step, img)
+    return np.clip(img, 0.0, 255.0).astype(np.float32)
+
+
+def moving_ellipses_volume(shape: Sequence[int], seed: int) -> np.ndarray:
+    """A video volume in [0, 255] (float32), frames along axis 0: a smooth background
+    and 6 ellipses that move at constant velocity (at most 1.5 pixels per frame),
+    each with a smooth intensity ramp that drifts slowly over time."""
+    n0, n1, n2 = (int(s) for s in shape)
+    r = _rng(seed)
+    y, x = np.meshgrid(np.arange(n1, dtype=np.float64), np.arange(n2, dtype=np.float64),
+                       indexing="ij")
+    m = float(max(n1, n2))
+    bg0 = r.uniform(60, 140)
+    bgy, bgx = r.uniform(-30, 30, size=2)
+    objs = []
+    for _ in range(6):
+        objs.append(dict(
+            cy=r.uniform(0, n1), cx=r.uniform(0, n2),
+            vy=r.uniform(-1.5, 1.5) / np.sqrt(2), vx=r.uniform(-1.5, 1.5) / np.sqrt(2),
+            ay=r.uniform(m / 12, m / 4), ax=r.uniform(m / 12, m / 4),
+            th=r.uniform(0, np.pi), val=r.uniform(20, 235),
+            gy=r.uniform(-1, 1), gx=r.uniform(-1, 1), dval=r.uniform(-0.3, 0.3)))
+    vol = np.empty((n0, n1, n2), dtype=np.float32)
+    for t in range(n0):
+        img = bg0 + bgy * (y / n1 - 0.5) + bgx * (x / n2 - 0.5)
+        for o in objs:
+            cy = (o["cy"] + o["vy"] * t) % n1
+            cx = (o["cx"] + o["vx"] * t) % n2
+            c, s = np.cos(o["th"]), np.sin(o["th"])
+            u = ((y - cy) * c + (x - cx) * s) / o["ay"]
+            v = (-(y - cy) * s + (x - cx) * c) / o["ax"]
+            inside = (u * u + v * v) <= 1.0
+            val = o["val"] + o["dval"] * t + 30.0 * (o["gy"] * (y - cy) + o["gx"] * (x - cx)) / m
+            img = np.where(inside, val, img)
+        vol[t] = np.clip(img, 0.0, 255.0)
+    return vol
+
+
+def add_noise(x: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """x + e with e ~ N(0, sigma^2) i.i.d. (Sec. 5.3); not clipped (float32)."""
+    r = _rng(seed)
+    return (np.asarray(x, dtype=np.float64)
+            + float(sigma) * r.standard_normal(np.shape(x))).astype(np.float32)
+
+
+def gaussian_field(shape: Sequence[int], seed: int, scale: float = 1.0) -> np.ndarray:
+    """i.i.d. N(0, scale^2) samples (float32), e.g. random coefficient stacks."""
+    return (float(scale) * _rng(seed).standard_normal(tuple(shape))).astype(np.float32)
+
+
+def uneven_batch_shapes(n: int, sides: Sequence[int], seed: int) -> List[Tuple[int, int]]:
+    """n image shapes (n0, n1) with each side drawn independently from ``sides``."""
+    r = _rng(seed)
+    s = np.asarray(list(sides))
+    return [(int(r.choice(s)), int(r.choice(s))) for _ in range(n)]
