@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the forward + inverse digital shearlet transform on one B300.
+
+Workload: one 512x512 float32 image (seeded piecewise-smooth cartoon + Gaussian noise,
+sigma = 20), four scales, shear levels (1, 1, 2, 2): R = 49 filters. One step is
+sl_forward (x -> 49 coefficient planes) followed by sl_inverse (planes -> x), with
+the filter bank built once beforehand. Metric: coefficients per second, R * N per
+step, aggregated over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 run under torch.distributed.run; every rank transforms its own image (no
+data exchange) and the time is the maximum over ranks. --impl reference times the
+FP64 CPU oracle on the host cores instead. Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (512, 512)
+J = 4
+LEVELS = (1, 1, 2, 2)
+SIGMA = 20.0
+METRIC = "fwd+inv shearlet coeffs/sec at stated error vs FP64 oracle; % of HBM roofline"
+UNIT = "coeffs/s"
+WORKLOAD = "2D 512x512 FP32 single image, nScales=4, shearLevels [1,1,2,2] (R=49), forward+inverse"
+SEED = 1402 + 1
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------- helpers ---
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def input_image(rank: int):
+    from paper_1402_5670_b300 import synth
+    clean = synth.piecewise_smooth_image(DIMS, SEED + rank)
+    return clean, synth.add_noise(clean, SIGMA, SEED + 1000 + rank)
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1402_5670_b300", "csrc")
+    for n in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, n), "rb") as f:
+            h.update(n.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None if
+    absent or taken on a different kernel source."""
+    try:
+        with open(TRAFFIC_PATH) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ our arm ---
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1402_5670_b300 import shearlet as S
+    from paper_1402_5670_b300.build import build
+
+    ws, rank, local = dist_env()
+    n_gpus = max(args.gpus, ws)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if ws > 1:
+        dist.barrier()
+    b = S.Bank(DIMS, J, LEVELS, device=local)
+    R, N = b.R, b.N
+    clean, noisy = input_image(rank)
+    x = torch.from_numpy(noisy).cuda()
+    C = torch.empty((R,) + DIMS, device="cuda")
+    y = torch.empty(DIMS, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        b.forward(x, out=C)
+        b.inverse(C, out=y)
+
+    step()
+    torch.cuda.synchronize()
+    # one launch per step: the step's kernels captured in a CUDA graph
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(args.warmup):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # L2 (126 MB) flushed between timed steps, outside the events
+        ev[k][0].record(stream)
+        graph.replay()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(bb) for a, bb in ev]
+    ms_step = sum(ms) / len(ms)
+    t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item())
+    value = R * N * n_gpus / (ms_step * 1e-3)
+
+    # accuracy of this run's output: reconstruction error against the input
+    rec_err = float((y - x).abs().max() / x.abs().max())
+
+    # end to end through the C ABI from pinned host memory (H2D, fwd, inv, D2H)
+    xh = torch.from_numpy(noisy).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(args.warmup):
+        b.fwdinv_host(xh, yh)
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        b.fwdinv_host(xh, yh)
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(bb) for a, bb in ev2) / args.steps
+    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    # per-kernel device time (events around every launch), same steps and flushes
+    S.sl_profile_reset()
+    S.sl_profile_enable(True)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = S.sl_profile_read()
+    S.sl_profile_enable(False)
+    S.sl_profile_reset()
+    launches_per_step = sum(v[0] for v in prof.values()) / args.steps
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_l, t_ms, by = prof[dom]
+    achieved = by / (t_ms * 1e-3) / 1e9 if by > 0 else 0.0
+    traffic = traffic_for(dom)
+    alg_step = 8 * N + 8 * R * N + 8 * R * b.Nh + 8 * b.Nh
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
+                   "share": v[1] / sum(w[1] for w in prof.values()),
+                   "alg_GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
+               for k, v in prof.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dims": list(DIMS), "nScales": J,
+                   "shearLevels": list(LEVELS), "R": R, "images_per_gpu": 1,
+                   "l2": "flushed between timed steps (512 MB write, outside the events)",
+                   "launch": "forward+inverse captured in one CUDA graph",
+                   "parallelism": f"replicas x{n_gpus}"},
+        "max_rel_err": {"reconstruction_vs_input": rec_err,
+                        "tolerance_vs_fp64_oracle": 1e-5,
+                        "checked_by": "tests/test_gpu_parity.py::test_full_size_2d_512"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.4 TB/s",
+                     "traffic": traffic, "alg_bytes_per_launch": by / n_l,
+                     "ms_per_launch": t_ms / n_l},
+        "roofline_step": {"alg_bytes": alg_step, "achieved_GBps": alg_step / (ms_step * 1e-3) / 1e9,
+                          "frac": alg_step / (ms_step * 1e-3) / 1e9 / peak},
+        "kernels": kernels,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": {"value": R * N * n_gpus / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+                "api": "sl_fwdinv_host (pinned host buffers)"},
+        "clocks": clk,
+    }
+    if n_gpus == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
+    print(json.dumps(line))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------- oracle on the host ---
+
+def _oracle_subset(sysm, js):
+    """A view of an oracle system restricted to filters js (same normalisation)."""
+    import copy
+    sub = copy.copy(sysm)
+    sub.meta = [sysm.meta[j] for j in js]
+    fn = sysm._filter_fn
+    sub._filter_fn = lambda i: fn(js[i])
+    sub._cache = {i: sysm._cache[j] for i, j in enumerate(js) if j in sysm._cache}
+    sub.norms = sysm.norms[list(js)]
+    return sub
+
+
+def cpu_baseline(budget_s: float):
+    """The FP64 oracle, as it stands, on this host: full 512x512 forward+inverse steps
+    (R = 49) until about budget_s seconds have been spent (after one untimed step)."""
+    import numpy as np
+    from oracle import shearlet_oracle as O
+    sysm = O.build_system(DIMS, J, LEVELS)
+    _, noisy = input_image(0)
+    x = noisy.astype(np.float64)
+    O.inverse(O.forward(x, sysm), sysm)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.inverse(O.forward(x, sysm), sysm)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sysm.R * sysm.N * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full forward+inverse steps of the 512x512 R=49 workload "
+                      f"({dt:.1f} s, numpy pocketfft, one thread)"}
+
+
+def run_reference(args):
+    import numpy as np
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import shearlet_oracle as O
+    sysm = O.build_system(DIMS, J, LEVELS)
+    _, noisy = input_image(0)
+    x = noisy.astype(np.float64)
+    # per-step sample sized so that the whole run takes about a minute
+    t0 = time.perf_counter()
+    O.inverse(O.forward(x, _oracle_subset(sysm, [0])), _oracle_subset(sysm, [0]))
+    per_filter = max(time.perf_counter() - t0, 1e-3)
+    nf = int(max(1, min(sysm.R, 60.0 / max(1, args.steps + args.warmup) / per_filter)))
+    js = list(range(0, sysm.R, max(1, sysm.R // nf)))[:nf]
+    sub = _oracle_subset(sysm, js)
+    for _ in range(args.warmup):
+        O.inverse(O.forward(x, sub), sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.inverse(O.forward(x, sub), sub)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = len(js) * sysm.N / (ms * 1e-3)
+    sample = (f"each step: forward+inverse of the 512x512 image restricted to {len(js)} of "
+              f"the {sysm.R} filters (every {max(1, sysm.R // nf)}th)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dims": list(DIMS), "nScales": J,
+                   "shearLevels": list(LEVELS), "R": sysm.R},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * libshearlet: B300-native (sm_103a) non-subsampled digital shearlet transform.
+ *
+ * The transform of ShearLab 3D (Kutyniok, Lim, Reisenhofer, arXiv 1402.5670) in the
+ * shift-invariant form of Sec. 3.4 (eq. convolution): for a real signal x on an
+ * n0 x n1 (2D) or n0 x n1 x n2 (3D) grid and a bank of R real, even filters psi_j,
+ *
+ *   forward   C_j = Re IFFT( FFT(x) * conj(psi_hat_j) )                j = 0..R-1
+ *   adjoint   x   = Re IFFT( sum_j FFT(C_j) * psi_hat_j )
+ *   inverse   x   = Re IFFT( sum_j FFT(C_j) * psi_hat_j / Psi )       (eq. reconstruction)
+ *             Psi = sum_j |psi_hat_j|^2                                (eq. frame_filter)
+ *   threshold C_j(m) kept iff |C_j(m)| >= K[s(j)] sigma ||psi_j||_2    (eq. hard_tresholding)
+ *
+ * Conventions for every call below.
+ *   Layout:    signals are contiguous row-major float32 arrays, last axis fastest
+ *              (x[i0][i1] or x[i0][i1][i2]). Coefficients are the stack C[R][dims]:
+ *              one contiguous plane/volume per filter, filter 0 (the lowpass) first.
+ *   Memory:    unless a name ends in _host, data pointers are DEVICE pointers on the
+ *              bank's device, owned by the caller; the library never frees them.
+ *              The library owns the bank, its filters and its scratch memory.
+ *   Streams:   `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *              stream). Calls are asynchronous on that stream; the caller
+ *              synchronises before reading results on the host.
+ *   Threading: calls on the same bank share its scratch memory: issue them on one
+ *              stream (or serialise them). Distinct banks are independent.
+ *   Errors:    every call returns an sl_status; nothing aborts the process and no
+ *              exception crosses this boundary. sl_last_error() describes the last
+ *              failure on the calling thread.
+ * Filter order (index j): 0 is the lowpass; then scales coarse to fine; within a
+ * scale cone 1 then cone 2 (2D) or pyramid 1, 2, 3 (3D), shears ascending
+ * (3D: k1 outer, k2 inner).
+ */
+#ifndef SHEARLET_H
+#define SHEARLET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SL_OK = 0,
+  SL_EINVAL = 1,    /* invalid argument: sizes, levels, null pointers, wrong device */
+  SL_ENOMEM = 2,    /* device or host allocation failed */
+  SL_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  SL_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  SL_ENOTSUP = 5,   /* valid request this build does not implement (e.g. a size) */
+  SL_ENAN = 6       /* non-finite values where finite ones are required */
+} sl_status;
+
+typedef struct sl_bank sl_bank; /* opaque; owned by the library */
+
+/* Human-readable name of a status code (static storage). */
+const char* sl_status_str(sl_status s);
+
+/* Text of the last error raised on the calling thread (static per-thread storage). */
+const char* sl_last_error(void);
+
+/*
+ * Build the digital shearlet filter bank on an N-grid, once (Algorithm 1 prologue;
+ * Sec. 4.3 "SLgetShearletSystem2D").
+ *   ndim         2 or 3.
+ *   dims         ndim sizes (host array), each a power of two in [8, 1024].
+ *   nScales      number of scales J >= 1 (Sec. 4.1 'nScales').
+ *   shearLevels  J entries d_j in [0, 4] (host array), coarse to fine (Sec. 4.1
+ *                'shearLevels'); scale j then has 2^(d_j+2) filters in 2D and
+ *                3(2 2^d+1)^2 - 6(2 2^d+1) + 4 in 3D (Sec. 4.4).
+ *   fullSystem   0: omit the boundary shearlets on the seams (Sec. 4.4); 1: keep them.
+ *   device       CUDA device ordinal that will run the transforms; -1 builds a
+ *                host-only bank (filters evaluable with sl_bank_eval_f64, no transforms).
+ *   out          receives the bank; free it with sl_free_filters.
+ * The filters are evaluated in FP64 on the host from their closed-form frequency
+ * responses (eqs. lowhigh, nonsep, dshear*_alpha, Defs. digitSH_alpha and
+ * 3DdigitSH_alpha), normalised so that max Psi = 1, and uploaded once: psi_hat as a
+ * real FP32 half spectrum, 1/Psi in FP64. Scratch memory for the transforms is
+ * allocated here. The calling thread's current device is set to `device`.
+ * Errors: SL_EINVAL (arguments), SL_ENOTSUP (sizes), SL_ENOMEM, SL_ECUDA.
+ */
+sl_status sl_build_filters(int ndim, const int64_t* dims, int nScales,
+                           const int* shearLevels, int fullSystem, int device,
+                           sl_bank** out);
+
+/* Release a bank and all library memory it holds. NULL is ignored. Call it with no
+ * transform of this bank still running on the GPU. */
+void sl_free_filters(sl_bank* bank);
+
+/* Shape of a bank: ndim, dims[0..ndim-1] (host array of 3), R (number of filters),
+ * nScales. Any output pointer may be NULL. */
+sl_status sl_bank_info(const sl_bank* bank, int* ndim, int64_t* dims, int* R,
+                       int* nScales);
+
+/* Per-filter metadata (host arrays of R entries; any may be NULL): scale_of[j] in
+ * 0..J-1 (-1 for the lowpass), cone_of[j] (2D cone 1/2, 3D pyramid 1..3, 0 for the
+ * lowpass), k_of[2j], k_of[2j+1] the shear(s) (2D: k and 0). */
+sl_status sl_bank_filter_meta(const sl_bank* bank, int* scale_of, int* cone_of,
+                              int* k_of);
+
+/* norms[j] = ||psi_j||_2 (host array of R, may be NULL) and the frame bounds
+ * A = min Psi, B = max Psi (= 1 after normalisation), FP64. */
+sl_status sl_bank_norms(const sl_bank* bank, double* norms, double* A, double* B);
+
+/* Number of half-spectrum points Nh = N / n_last * (n_last/2 + 1), and N. */
+sl_status sl_bank_sizes(const sl_bank* bank, int64_t* N, int64_t* Nh);
+
+/* Evaluate filter j in FP64 on the host (normalised psi_hat_j on the half spectrum,
+ * layout [n0][..][n_last/2+1]) into the host array out[Nh]. j = -1 writes Psi. */
+sl_status sl_bank_eval_f64(const sl_bank* bank, int j, double* out);
+
+/* Copy the device FP32 filter bank [R][Nh] into the host array out. */
+sl_status sl_bank_filters_f32(const sl_bank* bank, float* out);
+
+/*
+ * Forward transform (Algorithm 1 with the conjugation of eq. convolution):
+ * x[dims] -> coeffs[R][dims]. Device pointers. coeffs must not alias x.
+ */
+sl_status sl_forward(const sl_bank* bank, const float* x, float* coeffs, void* stream);
+
+/* Adjoint of sl_forward: coeffs[R][dims] -> x[dims] (Algorithm 2 with the filters
+ * psi_hat_j in place of the duals). */
+sl_status sl_adjoint(const sl_bank* bank, const float* coeffs, float* x, void* stream);
+
+/* Dual-frame inverse (eq. reconstruction, Algorithm 2): coeffs[R][dims] -> x[dims].
+ * The division by Psi is done in FP64. sl_inverse(sl_forward(x)) = x up to rounding. */
+sl_status sl_inverse(const sl_bank* bank, const float* coeffs, float* x, void* stream);
+
+/*
+ * Hard thresholding in place (eq. hard_tresholding, Sec. 5.3): for every filter
+ * j >= 1, C_j(m) = 0 unless |C_j(m)| >= K[scale(j)] * sigma * ||psi_j||_2. The lowpass
+ * is left as is. K is a host array of nScales entries, coarse to fine. The threshold
+ * is rounded to FP32 and compared in FP32 (a tie is kept).
+ */
+sl_status sl_threshold(const sl_bank* bank, float* coeffs, float sigma, const float* K,
+                       void* stream);
+
+/*
+ * Denoising x_out = T^-1 T_delta T x_noisy (Sec. 5.3) in one fused pass: the
+ * coefficients are thresholded as they are produced and never written to memory.
+ * noisy and out are device arrays [dims] (they may alias); K as in sl_threshold.
+ */
+sl_status sl_denoise(const sl_bank* bank, const float* noisy, float* out, float sigma,
+                     const float* K, void* stream);
+
+/*
+ * End-to-end round trip from HOST memory: copies x_host[dims] to the device,
+ * runs sl_forward into library-owned coefficient memory, then sl_inverse, and
+ * copies the reconstruction back to y_host[dims]. Host arrays should be pinned
+ * (cudaHostAlloc) for asynchronous copies. Returns after queuing; synchronise the
+ * stream before reading y_host.
+ */
+sl_status sl_fwdinv_host(const sl_bank* bank, const float* x_host, float* y_host,
+                         void* stream);
+
+/*
+ * Kernel timing for profiling. When enabled, every kernel launch of the library is
+ * bracketed by CUDA events recorded on the launch stream; sl_profile_read returns,
+ * per kernel kind, the number of launches, their summed device time (ms) and their
+ * summed algorithmic bytes (the DRAM traffic the transform needs in principle: the
+ * signal, the coefficients, the filters and 1/Psi, each counted once where it is
+ * read or written), after synchronising those events. Disabled by default; enabling
+ * it adds two event records per launch. Not for use inside stream capture.
+ */
+sl_status sl_profile_enable(int on);
+sl_status sl_profile_reset(void);
+/* Up to `cap` kinds: names[i] (valid until the next sl_profile_reset), launches[i],
+ * ms[i], bytes[i]; any array may be NULL. *count receives the number of kinds. */
+sl_status sl_profile_read(const char** names, int64_t* launches, double* ms, double* bytes,
+                          int cap, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHEARLET_H */

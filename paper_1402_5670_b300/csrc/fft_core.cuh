@@ -1,0 +1,131 @@
+// Register-resident small DFTs and the two-pass line-FFT decomposition used by every
+// transform kernel of libshearlet. Internal header.
+//
+// A length-L line is split as L = A * B (both powers of two). With n = a + A b and
+// k = kb + B ka,
+//   X[kb + B ka] = sum_a W_A^{a ka} * ( W_L^{a kb} * sum_b x[a + A b] W_B^{b kb} ).
+// Pass 1 gives each thread the B samples x[a + A b] of one (line, a): a DFT of length
+// B in registers, then the twiddle W_L^{a kb}. One exchange through shared memory
+// regroups the values by kb. Pass 2 gives each thread the A values of one (line, kb):
+// a DFT of length A in registers yields the outputs kb + B ka in natural order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <utility>
+
+namespace sl {
+namespace dev {
+
+// ------------------------------------------------------------------ complex ops ---
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * w for DIR < 0 (forward, w = e^{-i t}) and a * conj(w) for DIR > 0 (inverse).
+template <int DIR>
+__device__ __forceinline__ float2 ctw(float2 a, float2 w) {
+  if constexpr (DIR < 0) return cmul(a, w);
+  else return make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// ------------------------------------------------------- compile-time twiddles ---
+
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+
+// Taylor series, |x| <= pi: the truncation error of 20 terms is below 1e-25.
+constexpr double cx_sin(double x) {
+  double t = x, s = x;
+  for (int n = 1; n < 20; ++n) { t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0)); s += t; }
+  return s;
+}
+constexpr double cx_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int n = 1; n < 20; ++n) { t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n)); s += t; }
+  return s;
+}
+
+// W_N^K = exp(-2 pi i K / N) for 0 <= K < N/2 (angle in (-pi, 0]).
+template <int N, int K>
+struct Tw {
+  static constexpr float re = (float)cx_cos(-2.0 * kPiD * K / N);
+  static constexpr float im = (float)cx_sin(-2.0 * kPiD * K / N);
+};
+
+// ------------------------------------------------------------ register DFTs ---
+// In place, natural order in and out. DIR = -1: forward (e^{-i}), +1: inverse
+// (unnormalised). Radix-2 decimation in time, fully unrolled at compile time.
+
+template <int N, int DIR>
+struct Dft;
+
+template <int N, int DIR, int K>
+__device__ __forceinline__ void dft_bfly(float2 (&x)[N], const float2 (&e)[N / 2],
+                                         const float2 (&o)[N / 2]) {
+  float2 t;
+  if constexpr (K == 0) {
+    t = o[0];
+  } else if constexpr (4 * K == N) {  // W = -i (forward) or +i (inverse)
+    if constexpr (DIR < 0) t = make_float2(o[K].y, -o[K].x);
+    else t = make_float2(-o[K].y, o[K].x);
+  } else {
+    constexpr float wr = Tw<N, K>::re;
+    constexpr float wi = DIR < 0 ? Tw<N, K>::im : -Tw<N, K>::im;
+    t = make_float2(o[K].x * wr - o[K].y * wi, o[K].x * wi + o[K].y * wr);
+  }
+  x[K] = cadd(e[K], t);
+  x[K + N / 2] = csub(e[K], t);
+}
+
+template <int N, int DIR, int... K>
+__device__ __forceinline__ void dft_combine(float2 (&x)[N], const float2 (&e)[N / 2],
+                                            const float2 (&o)[N / 2],
+                                            std::integer_sequence<int, K...>) {
+  (dft_bfly<N, DIR, K>(x, e, o), ...);
+}
+
+template <int N, int DIR>
+struct Dft {
+  static __device__ __forceinline__ void run(float2 (&x)[N]) {
+    float2 e[N / 2], o[N / 2];
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      e[i] = x[2 * i];
+      o[i] = x[2 * i + 1];
+    }
+    Dft<N / 2, DIR>::run(e);
+    Dft<N / 2, DIR>::run(o);
+    dft_combine<N, DIR>(x, e, o, std::make_integer_sequence<int, N / 2>{});
+  }
+};
+
+template <int DIR>
+struct Dft<1, DIR> {
+  static __device__ __forceinline__ void run(float2 (&)[1]) {}
+};
+
+// ------------------------------------------------------------- line split ---
+
+template <int L>
+struct Split;
+template <> struct Split<8> { static constexpr int A = 4, B = 2; };
+template <> struct Split<16> { static constexpr int A = 4, B = 4; };
+template <> struct Split<32> { static constexpr int A = 8, B = 4; };
+template <> struct Split<64> { static constexpr int A = 8, B = 8; };
+template <> struct Split<128> { static constexpr int A = 16, B = 8; };
+template <> struct Split<256> { static constexpr int A = 16, B = 16; };
+template <> struct Split<512> { static constexpr int A = 32, B = 16; };
+template <> struct Split<1024> { static constexpr int A = 32, B = 32; };
+
+// Offset of the twiddle table of length L inside the concatenated table
+// (lengths 8, 16, ..., 1024 stored back to back): 8 + 16 + ... + L/2 = L - 8.
+__host__ __device__ constexpr int twiddle_offset(int L) { return L - 8; }
+constexpr int kTwiddleTotal = 2048 - 8;
+
+}  // namespace dev
+}  // namespace sl

@@ -1,0 +1,181 @@
+// 3D plane passes: transforms along axes 1 and 2 of one n1 x n2 plane held entirely in
+// shared memory (half spectrum along axis 2). Internal header.
+#pragma once
+
+#include "kernels2d.cuh"
+
+namespace sl {
+namespace dev {
+
+constexpr int kPlaneThreads = 512;
+
+template <int L1, int L2>
+struct PlaneGeom {
+  static constexpr int NH = L2 / 2 + 1;
+  static constexpr int HALF = L1 * NH;                                    // half plane
+  static constexpr int XROW = (L1 / 2) * Split<L2>::B * (Split<L2>::A + 1);  // row exchange
+  static constexpr int FULL = (L1 / 2) * L2;                               // row pairs, natural
+  static constexpr int S0 = HALF > XROW ? HALF : XROW;
+  static constexpr int S = S0 > FULL ? S0 : FULL;                         // one buffer
+  static constexpr int bytes = 2 * S * (int)sizeof(float2);
+};
+
+// FFT along axis 1 of a half plane [L1][NH] (columns), src -> wk (exchange) -> dst
+// (natural). src may equal dst. Ends with a __syncthreads().
+template <int L1, int NH, int DIR>
+__device__ __forceinline__ void plane_col_fft(const float2* src, float2* wk, float2* dst) {
+  constexpr int A = Split<L1>::A, B = Split<L1>::B;
+  const float2* tw = g_twiddle + twiddle_offset(L1);
+  for (int it = threadIdx.x; it < NH * A; it += kPlaneThreads) {
+    const int col = it % NH, a = it / NH;
+    float2 v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = src[(a + A * b) * NH + col];
+    Dft<B, DIR>::run(v);
+#pragma unroll
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<DIR>(v[kb], tw[kb * A + a]);
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) wk[(kb * A + a) * NH + col] = v[kb];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < NH * B; it += kPlaneThreads) {
+    const int col = it % NH, kb = it / NH;
+    float2 w[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) w[a] = wk[(kb * A + a) * NH + col];
+    Dft<A, DIR>::run(w);
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) dst[(kb + B * ka) * NH + col] = w[ka];
+  }
+  __syncthreads();
+}
+
+// Plane pass for slot blockIdx.y, plane blockIdx.x (axis-0 index i0).
+//   ROW_C2R  half-spectrum plane -> real plane * scale (optional threshold)
+//   ROW_R2C  real plane -> half-spectrum plane
+//   ROW_RT   half -> real * scale -> threshold -> half
+// in/out slot strides are in elements of their own type; one plane of a slot starts
+// at i0 * (L1 * NH) (half) or i0 * (L1 * L2) (real).
+template <int L1, int L2, int MODE>
+__global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
+  using G = PlaneGeom<L1, L2>;
+  constexpr int NH = G::NH;
+  constexpr int A = Split<L2>::A, B = Split<L2>::B;
+  constexpr int LS = B * (A + 1);
+  constexpr int PAIRS = L1 / 2;
+  constexpr int H = L2 / 2;
+  extern __shared__ float2 sm[];
+  float2* P = sm;
+  float2* W = sm + G::S;
+  const int tid = threadIdx.x;
+  const int slot = blockIdx.y, i0 = blockIdx.x;
+  const float2* tw = g_twiddle + twiddle_offset(L2);
+
+  if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
+    const float2* in = p.in_half + (int64_t)slot * p.in_stride + (int64_t)i0 * G::HALF;
+    for (int i = tid; i < G::HALF; i += kPlaneThreads) P[i] = in[i];
+    __syncthreads();
+    plane_col_fft<L1, NH, 1>(P, W, P);
+    // rows (2q, 2q+1): complex inverse DFT of the Hermitian-extended pair
+    for (int it = tid; it < PAIRS * A; it += kPlaneThreads) {
+      const int a = it % A, q = it / A;
+      const float2* r0 = P + (2 * q) * NH;
+      const float2* r1 = r0 + NH;
+      float2 v[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int n = a + A * b;
+        float2 ya, yb;
+        if (n <= H) {
+          ya = r0[n];
+          yb = r1[n];
+        } else {
+          ya = cconj(r0[L2 - n]);
+          yb = cconj(r1[L2 - n]);
+        }
+        v[b] = make_float2(ya.x - yb.y, ya.y + yb.x);
+      }
+      Dft<B, 1>::run(v);
+#pragma unroll
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a]);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = v[kb];
+    }
+    __syncthreads();
+    const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
+    float* outr = nullptr;
+    if constexpr (MODE == ROW_C2R)
+      outr = p.out_real + (int64_t)slot * p.out_stride + (int64_t)i0 * (L1 * L2);
+    for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
+      const int kb = it % B, q = it / B;
+      float2 w[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) w[a] = W[q * LS + kb * (A + 1) + a];
+      Dft<A, 1>::run(w);
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) {
+        const int k = kb + B * ka;
+        float c0 = w[ka].x * p.scale, c1 = w[ka].y * p.scale;
+        if (p.use_thr) {
+          if (fabsf(c0) < thr) c0 = 0.f;
+          if (fabsf(c1) < thr) c1 = 0.f;
+        }
+        if constexpr (MODE == ROW_C2R) {
+          outr[(2 * q) * L2 + k] = c0;
+          outr[(2 * q + 1) * L2 + k] = c1;
+        } else {
+          P[q * L2 + k] = make_float2(c0, c1);  // natural pairs for the forward pass
+        }
+      }
+    }
+    if constexpr (MODE == ROW_C2R) return;
+    __syncthreads();
+  }
+
+  // real rows (pairs) -> half rows in W -> FFT along axis 1 -> out
+  {
+    const float* inr = nullptr;
+    if constexpr (MODE == ROW_R2C)
+      inr = p.in_real + (int64_t)slot * p.in_stride + (int64_t)i0 * (L1 * L2);
+    for (int it = tid; it < PAIRS * A; it += kPlaneThreads) {
+      const int a = it % A, q = it / A;
+      float2 v[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int n = a + A * b;
+        if constexpr (MODE == ROW_R2C) v[b] = make_float2(inr[(2 * q) * L2 + n], inr[(2 * q + 1) * L2 + n]);
+        else v[b] = P[q * L2 + n];
+      }
+      Dft<B, -1>::run(v);
+#pragma unroll
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a]);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = v[kb];
+    }
+    __syncthreads();
+    for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
+      const int kb = it % B, q = it / B;
+      float2 w[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) w[a] = W[q * LS + kb * (A + 1) + a];
+      Dft<A, -1>::run(w);
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) P[q * L2 + kb + B * ka] = w[ka];
+    }
+    __syncthreads();
+    for (int it = tid; it < PAIRS * NH; it += kPlaneThreads) {
+      const int q = it / NH, k = it % NH;
+      const float2 z = P[q * L2 + k];
+      const float2 w = P[q * L2 + ((L2 - k) & (L2 - 1))];
+      W[(2 * q) * NH + k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
+      W[(2 * q + 1) * NH + k] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+    }
+    __syncthreads();
+    plane_col_fft<L1, NH, -1>(W, P, W);
+    float2* out = p.out_half + (int64_t)slot * p.out_stride + (int64_t)i0 * G::HALF;
+    for (int i = tid; i < G::HALF; i += kPlaneThreads) out[i] = W[i];
+  }
+}
+
+}  // namespace dev
+}  // namespace sl

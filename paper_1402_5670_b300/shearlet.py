@@ -1,0 +1,287 @@
+"""ctypes binding of libshearlet (include/shearlet.h): argument marshalling only.
+
+Every function here forwards to the C ABI function of the same name; the transform
+itself runs in the library's CUDA kernels. Device buffers are torch CUDA tensors
+(float32, contiguous); the stream is torch's current stream unless one is given.
+There is no fallback: if libshearlet.so is missing or fails to load, the import of
+this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libshearlet.so")
+
+SL_OK = 0
+STATUS = {0: "SL_OK", 1: "SL_EINVAL", 2: "SL_ENOMEM", 3: "SL_ECUDA", 4: "SL_ETIMEOUT",
+          5: "SL_ENOTSUP", 6: "SL_ENAN"}
+
+_c_int64_p = ctypes.POINTER(ctypes.c_int64)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_float_p = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); the declarations of include/shearlet.h
+SIGNATURES = {
+    "sl_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "sl_last_error": (ctypes.c_char_p, []),
+    "sl_build_filters": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
+                                        ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "sl_free_filters": (None, [_vp]),
+    "sl_bank_info": (ctypes.c_int, [_vp, _c_int_p, _c_int64_p, _c_int_p, _c_int_p]),
+    "sl_bank_filter_meta": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
+    "sl_bank_norms": (ctypes.c_int, [_vp, _c_double_p, _c_double_p, _c_double_p]),
+    "sl_bank_sizes": (ctypes.c_int, [_vp, _c_int64_p, _c_int64_p]),
+    "sl_bank_eval_f64": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p]),
+    "sl_bank_filters_f32": (ctypes.c_int, [_vp, _c_float_p]),
+    "sl_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_inverse": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_threshold": (ctypes.c_int, [_vp, _vp, ctypes.c_float, _c_float_p, _vp]),
+    "sl_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _c_float_p, _vp]),
+    "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "sl_profile_reset": (ctypes.c_int, []),
+    "sl_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), _c_int64_p,
+                                       _c_double_p, _c_double_p, ctypes.c_int, _c_int_p]),
+}
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+class ShearletError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libshearlet.so (built in-tree by paper_1402_5670_b300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1402_5670_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, where: str) -> None:
+    if status != SL_OK:
+        raise ShearletError(status, where, lib().sl_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dev_ptr(t, name: str, numel: int) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------- C ABI, same names ---
+
+def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
+                     full_system: bool = False, device: int = 0) -> int:
+    nd = len(dims)
+    d = (ctypes.c_int64 * nd)(*[int(v) for v in dims])
+    sl = (ctypes.c_int * len(shear_levels))(*[int(v) for v in shear_levels])
+    out = _vp()
+    _check(lib().sl_build_filters(nd, d, int(n_scales), sl, int(bool(full_system)), int(device),
+                                  ctypes.byref(out)), "sl_build_filters")
+    return out.value
+
+
+def sl_free_filters(bank: int) -> None:
+    lib().sl_free_filters(bank)
+
+
+def sl_forward(bank: int, x, coeffs, stream=None) -> None:
+    _check(lib().sl_forward(bank, x, coeffs, stream), "sl_forward")
+
+
+def sl_adjoint(bank: int, coeffs, x, stream=None) -> None:
+    _check(lib().sl_adjoint(bank, coeffs, x, stream), "sl_adjoint")
+
+
+def sl_inverse(bank: int, coeffs, x, stream=None) -> None:
+    _check(lib().sl_inverse(bank, coeffs, x, stream), "sl_inverse")
+
+
+def sl_threshold(bank: int, coeffs, sigma: float, K: Sequence[float], stream=None) -> None:
+    k = (ctypes.c_float * len(K))(*[float(v) for v in K])
+    _check(lib().sl_threshold(bank, coeffs, float(sigma), k, stream), "sl_threshold")
+
+
+def sl_denoise(bank: int, noisy, out, sigma: float, K: Sequence[float], stream=None) -> None:
+    k = (ctypes.c_float * len(K))(*[float(v) for v in K])
+    _check(lib().sl_denoise(bank, noisy, out, float(sigma), k, stream), "sl_denoise")
+
+
+def sl_fwdinv_host(bank: int, x_host, y_host, stream=None) -> None:
+    _check(lib().sl_fwdinv_host(bank, x_host, y_host, stream), "sl_fwdinv_host")
+
+
+def sl_profile_enable(on: bool) -> None:
+    _check(lib().sl_profile_enable(int(bool(on))), "sl_profile_enable")
+
+
+def sl_profile_reset() -> None:
+    _check(lib().sl_profile_reset(), "sl_profile_reset")
+
+
+def sl_profile_read(cap: int = 64) -> dict:
+    """{kernel kind: (launches, total ms, total algorithmic bytes)}"""
+    names = (ctypes.c_char_p * cap)()
+    launches = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    by = (ctypes.c_double * cap)()
+    cnt = ctypes.c_int()
+    _check(lib().sl_profile_read(names, launches, ms, by, cap, ctypes.byref(cnt)),
+           "sl_profile_read")
+    return {names[i].decode(): (int(launches[i]), float(ms[i]), float(by[i]))
+            for i in range(cnt.value)}
+
+
+# ------------------------------------------------------------ Bank object ---
+
+class Bank:
+    """A filter bank on one device (sl_build_filters) with the transforms bound to it.
+
+    device=-1 builds a host-only bank: its filters can be evaluated (eval_f64) but it
+    runs no transforms.
+    """
+
+    def __init__(self, dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
+                 full_system: bool = False, device: int = 0):
+        if device >= 0:
+            import torch
+            torch.cuda.set_device(device)
+        self.handle = sl_build_filters(dims, n_scales, shear_levels, full_system, device)
+        L = lib()
+        nd, R, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        dd = (ctypes.c_int64 * 3)()
+        _check(L.sl_bank_info(self.handle, ctypes.byref(nd), dd, ctypes.byref(R), ctypes.byref(J)),
+               "sl_bank_info")
+        self.ndim = nd.value
+        self.dims = tuple(int(dd[i]) for i in range(self.ndim))
+        self.R = R.value
+        self.n_scales = J.value
+        self.device = device
+        N, Nh = ctypes.c_int64(), ctypes.c_int64()
+        _check(L.sl_bank_sizes(self.handle, ctypes.byref(N), ctypes.byref(Nh)), "sl_bank_sizes")
+        self.N, self.Nh = N.value, Nh.value
+        self.norms = np.zeros(self.R)
+        A, B = ctypes.c_double(), ctypes.c_double()
+        _check(L.sl_bank_norms(self.handle, self.norms.ctypes.data_as(_c_double_p),
+                               ctypes.byref(A), ctypes.byref(B)), "sl_bank_norms")
+        self.A, self.B = A.value, B.value
+        self.scale_of = np.zeros(self.R, dtype=np.int32)
+        self.cone_of = np.zeros(self.R, dtype=np.int32)
+        self.k_of = np.zeros((self.R, 2), dtype=np.int32)
+        _check(L.sl_bank_filter_meta(self.handle, self.scale_of.ctypes.data_as(_c_int_p),
+                                     self.cone_of.ctypes.data_as(_c_int_p),
+                                     self.k_of.ctypes.data_as(_c_int_p)), "sl_bank_filter_meta")
+
+    @property
+    def half_shape(self):
+        return self.dims[:-1] + (self.dims[-1] // 2 + 1,)
+
+    def eval_f64(self, j: int) -> np.ndarray:
+        """Normalised psi_hat_j on the half spectrum (j = -1: Psi), FP64, on the host."""
+        out = np.zeros(self.Nh)
+        _check(lib().sl_bank_eval_f64(self.handle, int(j), out.ctypes.data_as(_c_double_p)),
+               "sl_bank_eval_f64")
+        return out.reshape(self.half_shape)
+
+    def filters_f32(self) -> np.ndarray:
+        out = np.zeros((self.R,) + self.half_shape, dtype=np.float32)
+        _check(lib().sl_bank_filters_f32(self.handle, out.ctypes.data_as(_c_float_p)),
+               "sl_bank_filters_f32")
+        return out
+
+    # -------- transforms (device tensors) --------
+
+    def _empty(self, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.float32, device=f"cuda:{self.device}")
+
+    def forward(self, x, out=None, stream=None):
+        out = self._empty((self.R,) + self.dims) if out is None else out
+        sl_forward(self.handle, _dev_ptr(x, "x", self.N), _dev_ptr(out, "coeffs", self.R * self.N),
+                   _stream_ptr(stream))
+        return out
+
+    def adjoint(self, coeffs, out=None, stream=None):
+        out = self._empty(self.dims) if out is None else out
+        sl_adjoint(self.handle, _dev_ptr(coeffs, "coeffs", self.R * self.N),
+                   _dev_ptr(out, "x", self.N), _stream_ptr(stream))
+        return out
+
+    def inverse(self, coeffs, out=None, stream=None):
+        out = self._empty(self.dims) if out is None else out
+        sl_inverse(self.handle, _dev_ptr(coeffs, "coeffs", self.R * self.N),
+                   _dev_ptr(out, "x", self.N), _stream_ptr(stream))
+        return out
+
+    def threshold_(self, coeffs, sigma: float, K: Sequence[float], stream=None):
+        self._check_K(K)
+        sl_threshold(self.handle, _dev_ptr(coeffs, "coeffs", self.R * self.N), sigma, K,
+                     _stream_ptr(stream))
+        return coeffs
+
+    def denoise(self, noisy, sigma: float, K: Sequence[float], out=None, stream=None):
+        self._check_K(K)
+        out = self._empty(self.dims) if out is None else out
+        sl_denoise(self.handle, _dev_ptr(noisy, "noisy", self.N), _dev_ptr(out, "out", self.N),
+                   sigma, K, _stream_ptr(stream))
+        return out
+
+    def fwdinv_host(self, x_host, y_host, stream=None):
+        """Round trip from host memory (x_host, y_host: pinned CPU float32 tensors)."""
+        for t, n in ((x_host, "x_host"), (y_host, "y_host")):
+            if t.is_cuda or t.numel() != self.N or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous CPU tensor of {self.N} floats")
+        sl_fwdinv_host(self.handle, x_host.data_ptr(), y_host.data_ptr(), _stream_ptr(stream))
+        return y_host
+
+    def _check_K(self, K):
+        if len(K) != self.n_scales:
+            raise ValueError(f"K needs {self.n_scales} entries (one per scale)")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sl_free_filters(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: 1e-5 relative (max-abs error over max-abs reference, per output array),
+the FP32 target of the transform. Threshold decisions are taken in FP32 on both sides
+(bit-exact); denoising is compared both against the oracle's inverse of the GPU's own
+FP32-thresholded coefficients and, by PSNR, against the oracle's full denoiser.
+"""
+import numpy as np
+import pytest
+
+from oracle import shearlet_oracle as O
+from paper_1402_5670_b300 import synth
+from tests.conftest import oracle_system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5670_b300.build import build
+    build()
+
+
+_BANKS = {}
+
+
+def bank(dims, J, sl, full=False):
+    from paper_1402_5670_b300.shearlet import Bank
+    key = (tuple(dims), J, tuple(sl), full)
+    if key not in _BANKS:
+        _BANKS[key] = Bank(dims, J, sl, full, device=0)
+    return _BANKS[key]
+
+
+def signal(dims, seed):
+    if len(dims) == 2:
+        x = synth.piecewise_smooth_image(dims, seed)
+    else:
+        x = synth.moving_ellipses_volume(dims, seed)
+    return synth.add_noise(x, 20.0, seed + 100)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+CASES_2D = [((16, 16), 1, (1,)), ((32, 32), 2, (0, 1)), ((64, 32), 2, (1, 1)),
+            ((32, 128), 2, (1, 2)), ((128, 256), 3, (1, 1, 2)), ((256, 256), 2, (1, 1)),
+            ((8, 8), 1, (0,)), ((1024, 64), 2, (1, 1))]
+CASES_3D = [((8, 8, 8), 1, (0,)), ((16, 16, 16), 2, (0, 1)), ((32, 16, 8), 2, (1, 1)),
+            ((16, 32, 64), 2, (1, 1)), ((64, 64, 64), 3, (0, 0, 1))]
+CASES = CASES_2D + CASES_3D
+
+
+@pytest.mark.parametrize("case", CASES, ids=str)
+def test_forward_matches_oracle(case):
+    dims, J, sl = case
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    x = signal(dims, 1)
+    C = b.forward(cuda(x)).cpu().numpy()
+    ref = O.forward(x.astype(np.float64), s)
+    assert rel(C, ref) < TOL
+    for j in (0, b.R // 2, b.R - 1):
+        assert rel(C[j], ref[j]) < 20 * TOL  # per subband, relative to its own size
+
+
+@pytest.mark.parametrize("case", CASES, ids=str)
+def test_inverse_and_adjoint_match_oracle(case):
+    dims, J, sl = case
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    x = signal(dims, 2)
+    C = O.forward(x.astype(np.float64), s).astype(np.float32)
+    Cg = cuda(C)
+    xi = b.inverse(Cg).cpu().numpy()
+    assert rel(xi, O.inverse(C.astype(np.float64), s)) < TOL
+    assert rel(xi, x) < TOL  # perfect reconstruction from FP32 coefficients
+    Cr = synth.gaussian_field((b.R,) + tuple(dims), 3)
+    xa = b.adjoint(cuda(Cr)).cpu().numpy()
+    assert rel(xa, O.adjoint(Cr.astype(np.float64), s)) < TOL
+
+
+@pytest.mark.parametrize("case", [CASES_2D[2], CASES_2D[5], CASES_3D[1]], ids=str)
+def test_threshold_bit_exact(case):
+    dims, J, sl = case
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    K = [2.5] * (J - 1) + [3.8]
+    x = signal(dims, 4)
+    C = O.forward(x.astype(np.float64), s).astype(np.float32)
+    Cg = cuda(C)
+    b.threshold_(Cg, 20.0, K)
+    ref = O.threshold(C, s, 20.0, K, dtype=np.float32)
+    assert np.array_equal(Cg.cpu().numpy(), ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("case", [CASES_2D[2], CASES_2D[5], CASES_3D[1], CASES_3D[2]], ids=str)
+def test_denoise_fused_matches_oracle(case):
+    dims, J, sl = case
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    K = [2.5] * (J - 1) + [3.8]
+    clean = (synth.piecewise_smooth_image(dims, 5) if len(dims) == 2
+             else synth.moving_ellipses_volume(dims, 5))
+    noisy = synth.add_noise(clean, 20.0, 6)
+    xg = cuda(noisy)
+    den = b.denoise(xg, 20.0, K).cpu().numpy()
+    # same FP32 decisions as the GPU: threshold the GPU's own coefficients
+    Cg = b.forward(xg)
+    b.threshold_(Cg, 20.0, K)
+    ref = O.inverse(Cg.cpu().numpy().astype(np.float64), s)
+    assert rel(den, ref) < TOL
+    # against the oracle's own FP64 denoiser: the same image quality
+    full = O.denoise(noisy.astype(np.float64), s, 20.0, K)
+    assert abs(O.psnr(clean, den) - O.psnr(clean, full)) < 0.01
+    assert O.psnr(clean, den) > O.psnr(clean, noisy)
+
+
+def test_fwdinv_host_round_trip():
+    dims = (256, 256)
+    b = bank(dims, 2, (1, 1))
+    x = signal(dims, 7)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    b.fwdinv_host(xh, yh)
+    torch.cuda.synchronize()
+    dev = b.inverse(b.forward(cuda(x))).cpu().numpy()
+    assert np.array_equal(yh.numpy(), dev)
+    assert rel(yh.numpy(), x) < TOL
+
+
+def test_zero_and_constant_inputs():
+    dims = (64, 64)
+    b = bank(dims, 3, (0, 1, 1))
+    z = torch.zeros(dims, device="cuda")
+    assert float(b.forward(z).abs().max()) == 0.0
+    c = torch.full(dims, 7.0, device="cuda")
+    C = b.forward(c)
+    s = oracle_system(dims, 3, (0, 1, 1))
+    assert rel(C.cpu().numpy(), O.forward(np.full(dims, 7.0), s)) < TOL
+    assert rel(b.inverse(C).cpu().numpy(), np.full(dims, 7.0)) < TOL
+
+
+def test_full_system_variant():
+    dims, J, sl = (64, 64), 2, (1, 2)
+    b = bank(dims, J, sl, True)
+    s = oracle_system(dims, J, sl, True)
+    x = signal(dims, 8)
+    C = b.forward(cuda(x)).cpu().numpy()
+    assert rel(C, O.forward(x.astype(np.float64), s)) < TOL
+    assert rel(b.inverse(cuda(C)).cpu().numpy(), x) < TOL
+
+
+def test_repeated_calls_are_deterministic():
+    dims = (128, 256)
+    b = bank(dims, 3, (1, 1, 2))
+    xg = cuda(signal(dims, 9))
+    C1 = b.forward(xg).clone()
+    C2 = b.forward(xg)
+    assert torch.equal(C1, C2)
+    assert torch.equal(b.inverse(C1), b.inverse(C2))
+
+
+# ------------------------------------------------ full-size configurations ---
+
+
+def test_full_size_2d_512():
+    """512^2, four scales, levels (1,1,2,2): R = 49 — the benchmark configuration,
+    compared element by element (forward, inverse, denoise)."""
+    dims, J, sl = (512, 512), 4, (1, 1, 2, 2)
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    assert b.R == 49
+    x = signal(dims, 10)
+    C = b.forward(cuda(x))
+    ref = O.forward(x.astype(np.float64), s)
+    assert rel(C.cpu().numpy(), ref) < TOL
+    xi = b.inverse(C).cpu().numpy()
+    assert rel(xi, O.inverse(C.cpu().numpy().astype(np.float64), s)) < TOL
+    assert rel(xi, x) < TOL
+
+
+def test_full_size_3d_128():
+    """128^3, three scales, levels (1,1,2): R = 292, sampled subbands against the
+    oracle (every 17th filter and the last), plus perfect reconstruction."""
+    dims, J, sl = (128, 128, 128), 3, (1, 1, 2)
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    assert b.R == 292
+    x = signal(dims, 11)
+    xg = cuda(x)
+    C = b.forward(xg)
+    X = np.fft.fftn(x.astype(np.float64))
+    scale = None
+    for j in list(range(0, b.R, 17)) + [b.R - 1]:
+        ref = np.real(np.fft.ifftn(X * s.psi_hat(j)))
+        got = C[j].cpu().numpy()
+        scale = np.max(np.abs(ref)) if j == 0 else scale
+        assert np.max(np.abs(got - ref)) / scale < TOL
+    xi = b.inverse(C).cpu().numpy()
+    assert rel(xi, x) < TOL
