@@ -152,6 +152,36 @@ sl_status sl_fwdinv_host(const sl_bank* bank, const float* x_host, float* y_host
                          void* stream);
 
 /*
+ * Allocation-free forward transform. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they transform, e.g.
+ * code running inside a fixed memory budget, a host callback, or an arena that some
+ * other component owns. It computes exactly what sl_forward computes, but calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch (the signal's
+ * spectrum and the per-filter intermediate spectra) lives in one static device array
+ * of SL_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library holds
+ * until the process exits.
+ *   bank    geometry and filter order; may be host-only (built with device = -1,
+ *           which allocates no device memory). Its own device memory, if any, is
+ *           not used.
+ *   psi     DEVICE array [R][Nh] of the normalised FP32 filter half spectra, owned by
+ *           the caller (e.g. sl_bank_filters_f32 or sl_bank_eval_f64, copied into
+ *           memory the caller already has).
+ *   x       DEVICE input [dims]; coeffs DEVICE output [R][dims] (must not alias x).
+ * Runs on the calling thread's current device. The first call on a device does a
+ * one-time set-up (looks up the static array's device address and uploads the FFT
+ * twiddle tables); make that first call before any stream capture. Every call
+ * shares the one array and leaves its contents behind; nothing in it has to start
+ * at zero (each call overwrites what it reads), but calls whose kernels overlap on
+ * the GPU (other streams, other threads) race on it: serialise them. Keep profiling
+ * (sl_profile_enable) off, since it creates events per launch.
+ * Errors: SL_EINVAL (NULL pointers); SL_ENOTSUP when 2 * Nh * 8 bytes exceed
+ * SL_NOALLOC_SCRATCH_BYTES (e.g. 3D 128^3); SL_ECUDA.
+ */
+#define SL_NOALLOC_SCRATCH_BYTES (16u << 20)
+sl_status sl_forward_noalloc(const sl_bank* bank, const float* psi, const float* x,
+                             float* coeffs, void* stream);
+
+/*
  * Kernel timing for profiling. When enabled, every kernel launch of the library is
  * bracketed by CUDA events recorded on the launch stream; sl_profile_read returns,
  * per kernel kind, the number of launches, their summed device time (ms) and their

@@ -804,3 +804,104 @@ sl_status sl_profile_read(const char** names, int64_t* launches, double* ms, dou
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- allocation-free forward ---
+// Scratch for sl_forward_noalloc: a file-scope device array instead of memory from
+// cudaMalloc. Host code must not use the symbol as an address; it asks the runtime
+// for the array's device address once per device (noalloc_scratch_ptr).
+
+static __device__ __align__(256) float2 g_noalloc_scratch[SL_NOALLOC_SCRATCH_BYTES / sizeof(float2)];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64] = {nullptr};
+
+static sl_status noalloc_scratch_ptr(int dev, float2** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (dev < 0 || dev >= 64) return fail(SL_EINVAL, "device ordinal out of range");
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<float2*>(g_noalloc_addr[dev]);
+  return SL_OK;
+}
+
+extern "C" sl_status sl_forward_noalloc(const sl_bank* b, const float* psi, const float* x,
+                                        float* coeffs, void* stream) {
+  if (!b) return fail(SL_EINVAL, "bank is NULL");
+  if (!psi || !x || !coeffs) return fail(SL_EINVAL, "psi, x or coeffs is NULL");
+  const int64_t cap = (int64_t)(SL_NOALLOC_SCRATCH_BYTES / sizeof(float2));
+  if (2 * b->Nh > cap)
+    return fail(SL_ENOTSUP, "sl_forward_noalloc: the signal's spectrum plus one filter's "
+                            "spectrum need " + std::to_string(2 * b->Nh * 8) +
+                            " bytes, more than SL_NOALLOC_SCRATCH_BYTES (16 MiB)");
+  int dev = -1;
+  SL_CUDA(cudaGetDevice(&dev));
+  SL_TRY(init_device(dev));
+  float2* xhat = nullptr;
+  SL_TRY(noalloc_scratch_ptr(dev, &xhat));
+  float2* slots = xhat + b->Nh;
+  const int G = (int)std::min<int64_t>({(cap - b->Nh) / b->Nh, (int64_t)kMaxGroup, (int64_t)b->R});
+  cudaStream_t st = (cudaStream_t)stream;
+  const sl::BankSpec& s = b->spec;
+  const int L0 = (int)s.dims[0];
+  const int NP = (int)(b->Nh / L0);
+  const int ctiles = (NP + col_tile(L0) - 1) / col_tile(L0);
+
+  // spectrum of x: last axes (rows or planes), then pencils along axis 0, in place
+  RowArgs ra{};
+  ra.in_real = x;
+  ra.out_half = xhat;
+  ra.scale = 1.f;
+  ra.nh = (int)s.nh();
+  ra.n_rows = L0;
+  if (s.ndim == 2) {
+    const int L1 = (int)s.dims[1];
+    dim3 g((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), 1);
+    SL_TRY(launched(launch_row<sl::dev::ROW_R2C>(L1, g, st, ra), "row_r2c"));
+  } else {
+    SL_TRY(launched(launch_plane<sl::dev::ROW_R2C>((int)s.dims[1], (int)s.dims[2], dim3(L0, 1),
+                                                   st, ra), "plane_r2c"));
+  }
+  ColArgs ca{};
+  ca.in = xhat;
+  ca.out = xhat;
+  ca.Nh = b->Nh;
+  ca.NP = NP;
+  SL_TRY(launched(launch_col<sl::dev::COL_SPEC>(L0, dim3(ctiles, 1), st, ca), "col_spec"));
+
+  // per group of G filters: pencils (x psi, inverse FFT) into the slots, then the
+  // last axes into the caller's coefficient planes
+  for (int j0 = 0; j0 < b->R; j0 += G) {
+    const int nf = std::min(G, b->R - j0);
+    ColArgs cf{};
+    cf.in = xhat;
+    cf.out = slots;
+    cf.psi = psi;
+    cf.Nh = b->Nh;
+    cf.NP = NP;
+    cf.j0 = j0;
+    cf.nfilt = nf;
+    SL_TRY(launched(launch_col<sl::dev::COL_FWD_FILT>(L0, dim3(ctiles, nf), st, cf),
+                    "col_fwd_filter"));
+    RowArgs rc{};
+    rc.in_half = slots;
+    rc.in_stride = b->Nh;
+    rc.out_real = coeffs + (int64_t)j0 * b->N;
+    rc.out_stride = b->N;
+    rc.scale = (float)(1.0 / (double)b->N);
+    rc.nh = (int)s.nh();
+    rc.n_rows = L0;
+    if (s.ndim == 2) {
+      const int L1 = (int)s.dims[1];
+      dim3 g((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), nf);
+      SL_TRY(launched(launch_row<sl::dev::ROW_C2R>(L1, g, st, rc), "row_c2r"));
+    } else {
+      SL_TRY(launched(launch_plane<sl::dev::ROW_C2R>((int)s.dims[1], (int)s.dims[2],
+                                                     dim3(L0, nf), st, rc), "plane_c2r"));
+    }
+  }
+  return SL_OK;
+}

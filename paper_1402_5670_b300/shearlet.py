@@ -46,6 +46,7 @@ SIGNATURES = {
     "sl_threshold": (ctypes.c_int, [_vp, _vp, ctypes.c_float, _c_float_p, _vp]),
     "sl_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _c_float_p, _vp]),
     "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sl_profile_reset": (ctypes.c_int, []),
     "sl_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), _c_int64_p,
@@ -140,6 +141,12 @@ def sl_denoise(bank: int, noisy, out, sigma: float, K: Sequence[float], stream=N
 
 def sl_fwdinv_host(bank: int, x_host, y_host, stream=None) -> None:
     _check(lib().sl_fwdinv_host(bank, x_host, y_host, stream), "sl_fwdinv_host")
+
+
+def sl_forward_noalloc(bank: int, psi, x, coeffs, stream=None) -> None:
+    """Forward transform that allocates nothing (static device scratch); psi, x and
+    coeffs are device pointers owned by the caller."""
+    _check(lib().sl_forward_noalloc(bank, psi, x, coeffs, stream), "sl_forward_noalloc")
 
 
 def sl_profile_enable(on: bool) -> None:
