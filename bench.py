@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--path", choices=["auto", "general", "cluster"], default="auto",
+                   help="kernel path of the library (auto: the one measured faster)")
     return p.parse_args()
 
 
@@ -164,7 +166,7 @@ def run_ours(args):
         build()
     if ws > 1:
         dist.barrier()
-    b = S.Bank(DIMS, J, LEVELS, device=local)
+    b = S.Bank(DIMS, J, LEVELS, device=local, path=args.path)
     R, N = b.R, b.N
     clean, noisy = input_image(rank)
     x = torch.from_numpy(noisy).cuda()
@@ -234,11 +236,14 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_ms = float(t.item())
 
-    # per-kernel device time (events around every launch), same steps and flushes
+    # per-kernel device time (events around every launch), same steps and flushes;
+    # a GPU-side sleep before each step lets the host queue the whole step first, so
+    # that the kernels run back to back and the events time the kernels, not the host
     S.sl_profile_reset()
     S.sl_profile_enable(True)
     for k in range(args.steps):
         flush.zero_()
+        torch.cuda._sleep(1_000_000)
         step()
     torch.cuda.synchronize()
     prof = S.sl_profile_read()
@@ -271,6 +276,7 @@ def run_ours(args):
                    "shearLevels": list(LEVELS), "R": R, "images_per_gpu": 1,
                    "l2": "flushed between timed steps (512 MB write, outside the events)",
                    "launch": "forward+inverse captured in one CUDA graph",
+                   "kernel_path": b.kernel_path,
                    "parallelism": f"replicas x{n_gpus}"},
         "max_rel_err": {"reconstruction_vs_input": rec_err,
                         "tolerance_vs_fp64_oracle": 1e-5,

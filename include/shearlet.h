@@ -81,6 +81,27 @@ sl_status sl_build_filters(int ndim, const int64_t* dims, int nScales,
                            const int* shearLevels, int fullSystem, int device,
                            sl_bank** out);
 
+/* Options of sl_build_filters_ex. Zero-initialise, then set what you need. */
+enum { SL_PATH_AUTO = 0, SL_PATH_GENERAL = 1, SL_PATH_CLUSTER = 2 };
+typedef struct {
+  /* Kernel path of sl_forward / sl_adjoint / sl_inverse:
+   *   SL_PATH_AUTO     the path measured faster on B300 (currently the general
+   *                    path everywhere);
+   *   SL_PATH_GENERAL  pencil pass along axis 0 and row/plane passes, with the
+   *                    per-filter intermediates in library scratch memory;
+   *   SL_PATH_CLUSTER  2D grids with both sides in [64, 512] only: one cluster of
+   *                    8 CTAs transforms a whole filter's spectrum in distributed
+   *                    shared memory (SL_ENOTSUP elsewhere).
+   * Both paths compute the same result. */
+  int path;
+  int reserved[7];
+} sl_options;
+
+/* sl_build_filters with options (opt may be NULL: defaults). */
+sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales,
+                              const int* shearLevels, int fullSystem, int device,
+                              const sl_options* opt, sl_bank** out);
+
 /* Release a bank and all library memory it holds. NULL is ignored. Call it with no
  * transform of this bank still running on the GPU. */
 void sl_free_filters(sl_bank* bank);
@@ -99,6 +120,10 @@ sl_status sl_bank_filter_meta(const sl_bank* bank, int* scale_of, int* cone_of,
 /* norms[j] = ||psi_j||_2 (host array of R, may be NULL) and the frame bounds
  * A = min Psi, B = max Psi (= 1 after normalisation), FP64. */
 sl_status sl_bank_norms(const sl_bank* bank, double* norms, double* A, double* B);
+
+/* The kernel path the bank's transforms take: SL_PATH_GENERAL or SL_PATH_CLUSTER
+ * (sl_denoise and sl_forward_noalloc always take the general path). */
+sl_status sl_bank_path(const sl_bank* bank, int* path);
 
 /* Number of half-spectrum points Nh = N / n_last * (n_last/2 + 1), and N. */
 sl_status sl_bank_sizes(const sl_bank* bank, int64_t* N, int64_t* Nh);
@@ -174,8 +199,9 @@ sl_status sl_fwdinv_host(const sl_bank* bank, const float* x_host, float* y_host
  * at zero (each call overwrites what it reads), but calls whose kernels overlap on
  * the GPU (other streams, other threads) race on it: serialise them. Keep profiling
  * (sl_profile_enable) off, since it creates events per launch.
- * Errors: SL_EINVAL (NULL pointers); SL_ENOTSUP when 2 * Nh * 8 bytes exceed
- * SL_NOALLOC_SCRATCH_BYTES (e.g. 3D 128^3); SL_ECUDA.
+ * Errors: SL_EINVAL (NULL pointers); SL_ENOTSUP when two spectra (the half spectrum
+ * padded to whole pencil tiles, 8 bytes per point) exceed SL_NOALLOC_SCRATCH_BYTES
+ * (e.g. 3D 128^3); SL_ECUDA.
  */
 #define SL_NOALLOC_SCRATCH_BYTES (16u << 20)
 sl_status sl_forward_noalloc(const sl_bank* bank, const float* psi, const float* x,

@@ -1,10 +1,18 @@
 // Transform kernels shared by the 2D and 3D paths: the pencil ("column") pass along
 // axis 0 and the 2D row passes along the last axis. Internal header.
 //
-// Spectra are stored as half spectra along the last axis, row-major: element
-// (k0, p) of a spectrum lives at k0 * NP + p, where p enumerates the NP points of one
-// slab (2D: NP = n1/2 + 1 columns; 3D: NP = n1 * (n2/2 + 1)). A stack of spectra
-// (one per filter of a group) is strided by Nh = n0 * NP.
+// Spectra (the signal's spectrum, the per-filter intermediates, the partial sums and
+// the filter bank itself) are half spectra along the last axis stored TILE-MAJOR: the
+// NP pencils of one spectrum (2D: the n1/2 + 1 columns; 3D: the n1 (n2/2 + 1) points of
+// a plane) are cut into tiles of TC consecutive pencils, and a tile is one contiguous
+// block [n0][TC]:
+//     element (k0, p)  ->  ((p / TC) * n0 + k0) * TC + p % TC.
+// A pencil-pass CTA therefore reads and writes one contiguous block per spectrum, and
+// a row (or plane) pass reads each row as runs of TC contiguous elements. The last
+// tile is padded to TC pencils. Pad pencils are transformed along with the others
+// but never read by a row or plane pass, so whatever they hold never reaches a
+// result (the bank stores zeros there). NPp = ceil(NP / TC) * TC and a spectrum holds
+// Nhp = n0 * NPp elements.
 #pragma once
 
 #include "fft_core.cuh"
@@ -12,7 +20,6 @@
 namespace sl {
 namespace dev {
 
-constexpr int kThreads = 256;
 constexpr int kMaxGroup = 256;  // filters per launch whose thresholds travel by value
 
 // Concatenated twiddle tables, one per line length L = 8..1024:
@@ -21,41 +28,71 @@ constexpr int kMaxGroup = 256;  // filters per launch whose thresholds travel by
 // exactly one translation unit).
 __device__ float2 g_twiddle[kTwiddleTotal];
 
-enum ColMode { COL_SPEC = 0, COL_FWD_FILT = 1, COL_INV_ACC = 2, COL_INV_FIN = 3 };
+// Lines (pencils or row pairs) per CTA. CTAs are kept small (128 threads) so that
+// several independent CTAs share an SM and overlap each other's memory latency.
+__host__ __device__ constexpr int col_tile_of(int L) {
+  return L == 8 ? 32 : L == 16 ? 32 : L == 32 ? 16 : L == 64 ? 16 : L == 128 ? 8 : L == 256 ? 8
+       : L == 512 ? 4 : 4;
+}
+
+// Line geometry: TC lines per CTA, T = TC * A threads (one pass-1 item per thread;
+// TC * B <= T threads take part in pass 2).
+template <int L>
+struct Geo {
+  static constexpr int A = Split<L>::A, B = Split<L>::B;
+  static constexpr int TC = col_tile_of(L);
+  static constexpr int T = TC * A;
+  // column exchange [B][A][TC] with the kb stride padded to XS = A*TC + PADX so that
+  // the lanes of a half-warp (16/TC values of kb, TC lines each) hit distinct banks
+  static constexpr int PADX = TC >= 16 ? 0 : TC;
+  static constexpr int XS = A * TC + PADX;
+  static constexpr int smem_col = B * XS * (int)sizeof(float2);
+  static constexpr int smem_row = TC * B * (A + 1) * (int)sizeof(float2);
+  static_assert(TC * B <= T, "pass 2 needs no more items than threads");
+};
+
+// Offset of element (k0, p) in a tile-major spectrum.
+struct TileMap {
+  int L0;   // pencil length n0
+  int lg;   // log2(TC)
+  __device__ __forceinline__ int64_t at(int k0, int p) const {
+    return ((int64_t)((p >> lg) * L0 + k0) << lg) + (p & ((1 << lg) - 1));
+  }
+};
+__device__ __forceinline__ int tm_tc(const TileMap& t) { return 1 << t.lg; }
+
+enum ColMode { COL_SPEC = 0, COL_FWD_FILT = 1, COL_INV_ACC = 2, COL_IFFT = 3 };
 
 struct ColArgs {
   const float2* in;
   float2* out;
-  const float* psi;      // [R][Nh] real half spectra
-  const double* invPsi;  // [Nh]
-  int64_t Nh;
-  int NP;                // pencils (columns) per spectrum
+  const float* psi;      // filters: tile-major [R][Nhp], or natural [R][Nh] (psi_natural)
+  int64_t Nhp;           // elements of one tile-major spectrum
+  int64_t Nh;            // elements of one natural half spectrum (psi_natural)
+  int NP;                // pencils per spectrum
+  int psi_natural;       // 1: psi is in natural layout [R][n0][NP]
   int j0;                // first filter of the group
   int nfilt;             // filters in the group
   int fps;               // filters per split (COL_INV_ACC)
   int part0;             // first partial written (COL_INV_ACC)
-  int nparts;            // partials summed (COL_INV_FIN)
-  int use_invpsi;        // COL_INV_FIN: 1 = divide by Psi (inverse), 0 = adjoint
 };
 
-// Pencil pass along axis 0 (length L = n0), TC = 256/B pencils per CTA.
-//   COL_SPEC      in-place forward FFT of a stack of 1 spectrum
+// Pencil pass along axis 0 (length L = n0); CTA blockIdx.x owns tile blockIdx.x.
+//   COL_SPEC      in-place forward FFT of one spectrum
 //   COL_FWD_FILT  slot s = blockIdx.y: out[s] = IFFT_0( in * psi[j0 + s] )
 //   COL_INV_ACC   split q = blockIdx.y: out[part0 + q] = sum_{j in split} psi[j] FFT_0(in[j - j0])
-//   COL_INV_FIN   out = IFFT_0( (sum_q in[q]) * invPsi )   (adjoint: without invPsi)
+//   COL_IFFT      in-place inverse FFT of one spectrum
 template <int L, int MODE>
-__global__ void __launch_bounds__(kThreads) k_col(ColArgs p) {
-  constexpr int A = Split<L>::A, B = Split<L>::B;
-  constexpr int TC = kThreads / B;
-  constexpr int IT1 = TC * A / kThreads;
+__global__ void __launch_bounds__(Geo<L>::T) k_col(ColArgs p) {
+  using G = Geo<L>;
+  constexpr int A = G::A, B = G::B, TC = G::TC;
   constexpr int DIR = (MODE == COL_SPEC || MODE == COL_INV_ACC) ? -1 : 1;
-  static_assert(TC * B == kThreads, "one pass-2 item per thread");
-  extern __shared__ float2 sm[];  // [B][A][TC]
+  constexpr int XS = G::XS;
+  extern __shared__ float2 sm[];  // [B][XS]: (kb, a, line) at kb * XS + a * TC + line
   const int tid = threadIdx.x;
-  const int pc0 = blockIdx.x * TC;
+  const int tile = blockIdx.x;
   const float2* tw = g_twiddle + twiddle_offset(L);
-  const int64_t Nh = p.Nh;
-  const int NP = p.NP;
+  const int64_t tbase = (int64_t)tile * L * TC;  // this CTA's block in a tile-major spectrum
 
   int jbeg = 0, jend = 1;
   if constexpr (MODE == COL_FWD_FILT) {
@@ -66,67 +103,53 @@ __global__ void __launch_bounds__(kThreads) k_col(ColArgs p) {
     jend = min(jbeg + p.fps, p.j0 + p.nfilt);
   }
 
-  // pass-2 item of this thread
+  // pass-1 item: (line, a); pass-2 item (tid < TC * B): (line2, kb2)
+  const int line = tid % TC, a = tid / TC;
   const int line2 = tid % TC, kb2 = tid / TC;
-  const int pc2 = pc0 + line2;
+  const bool in2 = tid < TC * B;
+  const int pc = tile * TC + line;  // global pencil index
   float2 acc[A];
 #pragma unroll
   for (int i = 0; i < A; ++i) acc[i] = make_float2(0.f, 0.f);
 
   for (int j = jbeg; j < jend; ++j) {
+    float2 v[B];
 #pragma unroll
-    for (int i = 0; i < IT1; ++i) {
-      const int it = tid + i * kThreads;
-      const int line = it % TC, a = it / TC;
-      const int pc = pc0 + line;
-      float2 v[B];
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const int n = a + A * b;
-        const int64_t e = (int64_t)n * NP + pc;
-        float2 val = make_float2(0.f, 0.f);
-        if (pc < NP) {
-          if constexpr (MODE == COL_SPEC) {
-            val = p.in[e];
-          } else if constexpr (MODE == COL_FWD_FILT) {
-            const float f = __ldg(p.psi + (int64_t)j * Nh + e);
-            val = cscale(__ldg(p.in + e), f);
-          } else if constexpr (MODE == COL_INV_ACC) {
-            val = p.in[(int64_t)(j - p.j0) * Nh + e];
-          } else {
-            float2 s = p.in[e];
-            for (int q = 1; q < p.nparts; ++q) s = cadd(s, p.in[(int64_t)q * Nh + e]);
-            if (p.use_invpsi) {
-              const double w = p.invPsi[e];
-              s = make_float2((float)((double)s.x * w), (float)((double)s.y * w));
-            }
-            val = s;
-          }
-        }
-        v[b] = val;
+    for (int b = 0; b < B; ++b) {
+      const int n = a + A * b;
+      const int64_t e = tbase + n * TC + line;
+      if constexpr (MODE == COL_SPEC || MODE == COL_IFFT) {
+        v[b] = p.in[e];
+      } else if constexpr (MODE == COL_FWD_FILT) {
+        float f;
+        if (p.psi_natural) f = pc < p.NP ? __ldg(p.psi + (int64_t)j * p.Nh + (int64_t)n * p.NP + pc) : 0.f;
+        else f = __ldg(p.psi + (int64_t)j * p.Nhp + e);
+        v[b] = cscale(__ldg(p.in + e), f);
+      } else {
+        v[b] = p.in[(int64_t)(j - p.j0) * p.Nhp + e];
       }
-      Dft<B, DIR>::run(v);
-#pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<DIR>(v[kb], tw[kb * A + a]);
-#pragma unroll
-      for (int kb = 0; kb < B; ++kb) sm[(kb * A + a) * TC + line] = v[kb];
     }
-    __syncthreads();
-    float2 w[A];
+    Dft<B, DIR>::run(v);
 #pragma unroll
-    for (int a = 0; a < A; ++a) w[a] = sm[(kb2 * A + a) * TC + line2];
-    Dft<A, DIR>::run(w);
-    if (pc2 < NP) {
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<DIR>(v[kb], tw[kb * A + a]);
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) sm[kb * XS + a * TC + line] = v[kb];
+    __syncthreads();
+    if (in2) {
+      float2 w[A];
+#pragma unroll
+      for (int aa = 0; aa < A; ++aa) w[aa] = sm[kb2 * XS + aa * TC + line2];
+      Dft<A, DIR>::run(w);
 #pragma unroll
       for (int ka = 0; ka < A; ++ka) {
         const int k = kb2 + B * ka;
-        const int64_t e = (int64_t)k * NP + pc2;
-        if constexpr (MODE == COL_SPEC || MODE == COL_INV_FIN) {
+        const int64_t e = tbase + k * TC + line2;
+        if constexpr (MODE == COL_SPEC || MODE == COL_IFFT) {
           p.out[e] = w[ka];
         } else if constexpr (MODE == COL_FWD_FILT) {
-          p.out[(int64_t)(j - p.j0) * Nh + e] = w[ka];
+          p.out[(int64_t)(j - p.j0) * p.Nhp + e] = w[ka];
         } else {
-          const float f = __ldg(p.psi + (int64_t)j * Nh + e);
+          const float f = __ldg(p.psi + (int64_t)j * p.Nhp + e);
           acc[ka].x = fmaf(f, w[ka].x, acc[ka].x);
           acc[ka].y = fmaf(f, w[ka].y, acc[ka].y);
         }
@@ -135,17 +158,133 @@ __global__ void __launch_bounds__(kThreads) k_col(ColArgs p) {
     __syncthreads();
   }
   if constexpr (MODE == COL_INV_ACC) {
-    if (pc2 < NP) {
-      float2* o = p.out + (int64_t)(p.part0 + blockIdx.y) * Nh;
+    if (in2) {
+      float2* o = p.out + (int64_t)(p.part0 + blockIdx.y) * p.Nhp;
 #pragma unroll
-      for (int ka = 0; ka < A; ++ka) o[(int64_t)(kb2 + B * ka) * NP + pc2] = acc[ka];
+      for (int ka = 0; ka < A; ++ka) o[tbase + (kb2 + B * ka) * TC + line2] = acc[ka];
     }
   }
 }
 
+// ------------------------------------------------------ pipelined pencil pass ---
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copy `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory with every thread of the CTA issuing 16-byte asynchronous copies.
+template <int T>
+__device__ __forceinline__ void cp_async_block(void* dst, const void* src, int bytes) {
+  char* d = static_cast<char*>(dst);
+  const char* s = static_cast<const char*>(src);
+  for (int o = threadIdx.x * 16; o < bytes; o += T * 16) cp_async16(d + o, s + o);
+}
+
+// Forward filter pass as a persistent, software-pipelined kernel: work item i is
+// (tile i / nfilt, filter j0 + i % nfilt); CTA c takes items c, c + gridDim.x, ...
+// While item k is transformed, the signal and filter tiles of item k + 1 stream into
+// the other shared-memory stage with cp.async, so global-memory latency overlaps
+// with the FFT. Output as COL_FWD_FILT: out[s] = IFFT_0(in * psi[j0 + s]).
 template <int L>
-constexpr int col_smem_bytes() {
-  return Split<L>::B * Split<L>::A * (kThreads / Split<L>::B) * (int)sizeof(float2);
+__global__ void __launch_bounds__(Geo<L>::T) k_col_fwd_pipe(ColArgs p) {
+  using G = Geo<L>;
+  constexpr int A = G::A, B = G::B, TC = G::TC, T = G::T, XS = G::XS;
+  constexpr int TILE = L * TC;  // elements of one tile
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* xs = reinterpret_cast<float2*>(smraw);                 // [2][TILE]
+  float* ps = reinterpret_cast<float*>(xs + 2 * TILE);           // [2][TILE]
+  float2* ex = reinterpret_cast<float2*>(ps + 2 * TILE);         // [B][XS]
+  const int tid = threadIdx.x;
+  const float2* tw = g_twiddle + twiddle_offset(L);
+  const int nitems = (int)(p.Nhp / TILE) * p.nfilt;  // tiles x filters
+  const int line = tid % TC, a = tid / TC;
+  const int line2 = tid % TC, kb2 = tid / TC;
+  const bool in2 = tid < TC * B;
+
+  auto issue = [&](int item, int stage) {
+    if (item < nitems) {
+      const int tile = item / p.nfilt, j = p.j0 + item % p.nfilt;
+      cp_async_block<T>(xs + stage * TILE, p.in + (int64_t)tile * TILE, TILE * 8);
+      cp_async_block<T>(ps + stage * TILE, p.psi + (int64_t)j * p.Nhp + (int64_t)tile * TILE,
+                        TILE * 4);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  issue(item, 0);
+  issue(item + gridDim.x, 1);
+  for (int k = 0; item < nitems; ++k, item += gridDim.x) {
+    const int stage = k & 1;
+    cp_async_wait<1>();
+    __syncthreads();
+    const int tile = item / p.nfilt, s = item % p.nfilt;
+    float2 v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int e = (a + A * b) * TC + line;
+      v[b] = cscale(xs[stage * TILE + e], ps[stage * TILE + e]);
+    }
+    Dft<B, 1>::run(v);
+#pragma unroll
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a]);
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) ex[kb * XS + a * TC + line] = v[kb];
+    __syncthreads();                        // stage and exchange inputs consumed
+    issue(item + 2 * gridDim.x, stage);     // prefetch two items ahead
+    if (in2) {
+      float2 w[A];
+#pragma unroll
+      for (int aa = 0; aa < A; ++aa) w[aa] = ex[kb2 * XS + aa * TC + line2];
+      Dft<A, 1>::run(w);
+      float2* o = p.out + (int64_t)s * p.Nhp + (int64_t)tile * TILE;
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) o[(kb2 + B * ka) * TC + line2] = w[ka];
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int L>
+constexpr int col_pipe_smem_bytes() {
+  return 2 * L * Geo<L>::TC * (8 + 4) + Geo<L>::B * Geo<L>::XS * 8;
+}
+
+// out[e] = (sum_q parts[q][e]) * w[e] (w in FP64, or 1 when w == nullptr), over one
+// tile-major spectrum of n float2 elements, two elements per thread and step.
+__global__ void __launch_bounds__(256) k_reduce_parts(const float2* __restrict__ parts, int nparts,
+                                                      int64_t stride, const double* __restrict__ w,
+                                                      float2* __restrict__ out, int64_t n) {
+  const int64_t n2 = n / 2;
+  const float4* p4 = reinterpret_cast<const float4*>(parts);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  const int64_t s4 = stride / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 s = p4[i];
+    for (int q = 1; q < nparts; ++q) {
+      const float4 t = p4[q * s4 + i];
+      s.x += t.x;
+      s.y += t.y;
+      s.z += t.z;
+      s.w += t.w;
+    }
+    if (w) {
+      const double w0 = w[2 * i], w1 = w[2 * i + 1];
+      s = make_float4((float)((double)s.x * w0), (float)((double)s.y * w0),
+                      (float)((double)s.z * w1), (float)((double)s.w * w1));
+    }
+    o4[i] = s;
+  }
 }
 
 // ------------------------------------------------------------------- row passes ---
@@ -158,12 +297,12 @@ struct Thresholds {
 
 struct RowArgs {
   const float* in_real;   // ROW_R2C: real rows, slot stride in_stride
-  const float2* in_half;  // ROW_C2R / ROW_RT: half-spectrum rows, slot stride in_stride
+  const float2* in_half;  // ROW_C2R / ROW_RT: tile-major spectra, slot stride in_stride
   float* out_real;        // ROW_C2R: real rows, slot stride out_stride
-  float2* out_half;       // ROW_R2C / ROW_RT: half rows, slot stride out_stride
+  float2* out_half;       // ROW_R2C / ROW_RT: tile-major spectra, slot stride out_stride
   int64_t in_stride, out_stride;
-  int n_rows;             // rows per slot (even)
-  int nh;                 // L/2 + 1
+  int n_rows;             // rows per slot (even) = n0
+  TileMap tm;             // layout of the spectra (L0 = n0, TC of the pencil pass)
   float scale;            // ROW_C2R / ROW_RT: factor on the real output
   int use_thr;
   Thresholds thr;         // per slot: keep |c| >= thr (ROW_C2R / ROW_RT)
@@ -173,51 +312,43 @@ struct RowArgs {
 //   ROW_R2C  real rows -> half spectra (unnormalised forward DFT)
 //   ROW_C2R  half spectra -> real rows (inverse DFT) * scale, optional threshold
 //   ROW_RT   half spectra -> real rows * scale -> threshold -> half spectra
-// PAIRS = 256/B row pairs per CTA; blockIdx.y is the slot.
-template <int L, int MODE>
-__global__ void __launch_bounds__(kThreads) k_row(RowArgs p) {
-  constexpr int A = Split<L>::A, B = Split<L>::B;
-  constexpr int PAIRS = kThreads / B;
-  constexpr int IT1 = PAIRS * A / kThreads;
+// PAIRS row pairs per CTA (T = PAIRS * A threads); blockIdx.y is the slot.
+template <int L, int MODE, int PAIRS>
+__global__ void __launch_bounds__(PAIRS * Split<L>::A) k_row(RowArgs p) {
+  constexpr int A = Split<L>::A, B = Split<L>::B, T = PAIRS * A;
   constexpr int LS = B * (A + 1);  // padded exchange stride per line
   constexpr int H = L / 2;
-  static_assert(PAIRS * B == kThreads, "one pass-2 item per thread");
   extern __shared__ float2 sm[];  // PAIRS * LS float2
   const int tid = threadIdx.x;
   const int slot = blockIdx.y;
   const int pair0 = blockIdx.x * PAIRS;
   const int npairs = p.n_rows / 2;
   const float2* tw = g_twiddle + twiddle_offset(L);
-  const int nh = p.nh;
+  const TileMap tm = p.tm;
 
-  const int kb2 = tid % B, line2 = tid / B;
+  const int a1 = tid % A, line1 = tid / A;  // pass-1 item
+  const int pr1 = pair0 + line1;
+  const int kb2 = tid % B, line2 = tid / B;  // pass-2 item (tid < PAIRS * B)
+  const bool in2 = tid < PAIRS * B;
   const int pr2 = pair0 + line2;
-  const bool ok2 = pr2 < npairs;
   float2 res[A];
 
   // ---------------------------------------------------------- half -> real ---
   if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
     const float2* in = p.in_half + (int64_t)slot * p.in_stride;
-#pragma unroll
-    for (int i = 0; i < IT1; ++i) {
-      const int it = tid + i * kThreads;
-      const int a = it % A, line = it / A;
-      const int pr = pair0 + line;
+    {
       float2 v[B];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
-        const int n = a + A * b;
+        const int n = a1 + A * b;
         float2 z = make_float2(0.f, 0.f);
-        if (pr < npairs) {
-          const float2* r0 = in + (int64_t)(2 * pr) * nh;
-          const float2* r1 = r0 + nh;
-          float2 ya, yb;
-          if (n <= H) {
-            ya = r0[n];
-            yb = r1[n];
-          } else {
-            ya = cconj(r0[L - n]);
-            yb = cconj(r1[L - n]);
+        if (pr1 < npairs) {
+          const int m = n <= H ? n : L - n;
+          float2 ya = in[tm.at(2 * pr1, m)];
+          float2 yb = in[tm.at(2 * pr1 + 1, m)];
+          if (n > H) {
+            ya = cconj(ya);
+            yb = cconj(yb);
           }
           z = make_float2(ya.x - yb.y, ya.y + yb.x);  // ya + i yb
         }
@@ -225,26 +356,28 @@ __global__ void __launch_bounds__(kThreads) k_row(RowArgs p) {
       }
       Dft<B, 1>::run(v);
 #pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a]);
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a1]);
 #pragma unroll
-      for (int kb = 0; kb < B; ++kb) sm[line * LS + kb * (A + 1) + a] = v[kb];
+      for (int kb = 0; kb < B; ++kb) sm[line1 * LS + kb * (A + 1) + a1] = v[kb];
     }
     __syncthreads();
-#pragma unroll
-    for (int a = 0; a < A; ++a) res[a] = sm[line2 * LS + kb2 * (A + 1) + a];
-    Dft<A, 1>::run(res);
     const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
+    if (in2) {
 #pragma unroll
-    for (int ka = 0; ka < A; ++ka) {
-      float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
-      if (p.use_thr) {
-        if (fabsf(c0) < thr) c0 = 0.f;
-        if (fabsf(c1) < thr) c1 = 0.f;
+      for (int aa = 0; aa < A; ++aa) res[aa] = sm[line2 * LS + kb2 * (A + 1) + aa];
+      Dft<A, 1>::run(res);
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) {
+        float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
+        if (p.use_thr) {
+          if (fabsf(c0) < thr) c0 = 0.f;
+          if (fabsf(c1) < thr) c1 = 0.f;
+        }
+        res[ka] = make_float2(c0, c1);
       }
-      res[ka] = make_float2(c0, c1);
     }
     if constexpr (MODE == ROW_C2R) {
-      if (ok2) {
+      if (in2 && pr2 < npairs) {
         float* o0 = p.out_real + (int64_t)slot * p.out_stride + (int64_t)(2 * pr2) * L;
         float* o1 = o0 + L;
 #pragma unroll
@@ -258,79 +391,341 @@ __global__ void __launch_bounds__(kThreads) k_row(RowArgs p) {
     }
     // ROW_RT: hand the thresholded rows to the forward pass through shared memory
     __syncthreads();
+    if (in2) {
 #pragma unroll
-    for (int ka = 0; ka < A; ++ka) sm[line2 * L + kb2 + B * ka] = res[ka];
+      for (int ka = 0; ka < A; ++ka) sm[line2 * L + kb2 + B * ka] = res[ka];
+    }
     __syncthreads();
   }
 
   // ---------------------------------------------------------- real -> half ---
   {
-    float2 v[IT1][B];
+    float2 v[B];
 #pragma unroll
-    for (int i = 0; i < IT1; ++i) {
-      const int it = tid + i * kThreads;
-      const int a = it % A, line = it / A;
-      const int pr = pair0 + line;
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const int n = a + A * b;
-        if constexpr (MODE == ROW_R2C) {
-          float2 z = make_float2(0.f, 0.f);
-          if (pr < npairs) {
-            const float* r0 = p.in_real + (int64_t)slot * p.in_stride + (int64_t)(2 * pr) * L;
-            z = make_float2(r0[n], r0[L + n]);
-          }
-          v[i][b] = z;
-        } else {
-          v[i][b] = sm[line * L + n];
+    for (int b = 0; b < B; ++b) {
+      const int n = a1 + A * b;
+      if constexpr (MODE == ROW_R2C) {
+        float2 z = make_float2(0.f, 0.f);
+        if (pr1 < npairs) {
+          const float* r0 = p.in_real + (int64_t)slot * p.in_stride + (int64_t)(2 * pr1) * L;
+          z = make_float2(r0[n], r0[L + n]);
         }
+        v[b] = z;
+      } else {
+        v[b] = sm[line1 * L + n];
       }
     }
     if constexpr (MODE == ROW_RT) __syncthreads();
+    Dft<B, -1>::run(v);
 #pragma unroll
-    for (int i = 0; i < IT1; ++i) {
-      const int it = tid + i * kThreads;
-      const int a = it % A, line = it / A;
-      Dft<B, -1>::run(v[i]);
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a1]);
 #pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[i][kb] = ctw<-1>(v[i][kb], tw[kb * A + a]);
-#pragma unroll
-      for (int kb = 0; kb < B; ++kb) sm[line * LS + kb * (A + 1) + a] = v[i][kb];
-    }
+    for (int kb = 0; kb < B; ++kb) sm[line1 * LS + kb * (A + 1) + a1] = v[kb];
   }
   __syncthreads();
+  if (in2) {
 #pragma unroll
-  for (int a = 0; a < A; ++a) res[a] = sm[line2 * LS + kb2 * (A + 1) + a];
-  Dft<A, -1>::run(res);
+    for (int aa = 0; aa < A; ++aa) res[aa] = sm[line2 * LS + kb2 * (A + 1) + aa];
+    Dft<A, -1>::run(res);
+  }
   __syncthreads();
+  if (in2) {
 #pragma unroll
-  for (int ka = 0; ka < A; ++ka) sm[line2 * L + kb2 + B * ka] = res[ka];
+    for (int ka = 0; ka < A; ++ka) sm[line2 * L + kb2 + B * ka] = res[ka];
+  }
   __syncthreads();
   // Split Z = FFT(x0 + i x1) into the half spectra of x0 and x1.
   float2* out = p.out_half + (int64_t)slot * p.out_stride;
   constexpr int HP = H + 1;
-  for (int it = tid; it < PAIRS * HP; it += kThreads) {
+  for (int it = tid; it < PAIRS * HP; it += T) {
     const int line = it / HP, k = it % HP;
     const int pr = pair0 + line;
     if (pr >= npairs) continue;
     const float2 z = sm[line * L + k];
     const float2 w = sm[line * L + ((L - k) & (L - 1))];
-    float2* o0 = out + (int64_t)(2 * pr) * nh;
-    o0[k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
-    o0[nh + k] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+    out[tm.at(2 * pr, k)] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
+    out[tm.at(2 * pr + 1, k)] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
   }
 }
 
+// ------------------------------------------------------- pipelined row passes ---
+
+// Row passes over many slots as a persistent, software-pipelined kernel: work item i
+// is (slot i / G, row-pair group i % G) with G = n_rows / (2 PAIRS); CTA c takes items
+// c, c + gridDim.x, ... and streams the next item's input rows into the other
+// shared-memory stage with cp.async while it transforms the current one.
+//   ROW_C2R: input tile-major half spectra (whole tile runs of NPp = ntiles*TC0 points
+//            per row are copied), output real rows (* scale, optional threshold).
+//   ROW_R2C: input real rows (one contiguous block per item), output tile-major half
+//            spectra.
+//   ROW_RT : C2R, threshold, R2C (input and output tile-major; may be in place).
+template <int L, int MODE, int PAIRS>
+struct RowPipe {
+  static constexpr int A = Split<L>::A, B = Split<L>::B, T = PAIRS * A;
+  static constexpr int LS = B * (A + 1);
+  static constexpr int XB = PAIRS * LS * 8;  // exchange bytes (>= PAIRS * L * 8)
+};
+
+template <int L, int MODE, int PAIRS>
+__global__ void __launch_bounds__(PAIRS * Split<L>::A)
+    k_row_pipe(RowArgs p, int nslots, int NPp, int stage_bytes) {
+  using RP = RowPipe<L, MODE, PAIRS>;
+  constexpr int A = RP::A, B = RP::B, T = RP::T, LS = RP::LS;
+  constexpr int H = L / 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* stg = smraw;                                        // [2][stage_bytes]
+  float2* sm = reinterpret_cast<float2*>(smraw + 2 * stage_bytes);  // exchange
+  const int tid = threadIdx.x;
+  const float2* tw = g_twiddle + twiddle_offset(L);
+  const TileMap tm = p.tm;
+  const int groups = p.n_rows / (2 * PAIRS);
+  const int nitems = groups * nslots;
+  const int a1 = tid % A, line1 = tid / A;
+  const int kb2 = tid % B, line2 = tid / B;
+  const bool in2 = tid < PAIRS * B;
+  const int nrun = NPp / tm_tc(tm);  // tile runs per row
+
+  auto issue = [&](int item, int stage) {
+    if (item < nitems) {
+      const int slot = item / groups, r0 = (item % groups) * 2 * PAIRS;
+      unsigned char* dst = stg + stage * stage_bytes;
+      if constexpr (MODE == ROW_R2C) {
+        const float* src = p.in_real + (int64_t)slot * p.in_stride + (int64_t)r0 * L;
+        for (int o = tid * 16; o < 2 * PAIRS * L * 4; o += T * 16)
+          cp_async16(dst + o, reinterpret_cast<const char*>(src) + o);
+      } else {
+        const float2* src = p.in_half + (int64_t)slot * p.in_stride;
+        const int tc = tm_tc(tm);
+        const int chunks = tc / 2;  // 16-byte chunks per tile run
+        const int per_row = nrun * chunks;
+        for (int c = tid; c < 2 * PAIRS * per_row; c += T) {
+          const int rr = c / per_row, rem = c % per_row;
+          const int t = rem / chunks, ch = rem % chunks;
+          const float2* g = src + (((int64_t)t * tm.L0 + r0 + rr) << tm.lg) + 2 * ch;
+          cp_async16(dst + ((int64_t)rr * NPp + t * tc + 2 * ch) * 8, g);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  issue(item, 0);
+  issue(item + gridDim.x, 1);
+  for (int k = 0; item < nitems; ++k, item += gridDim.x) {
+    const int stage = k & 1;
+    const int slot = item / groups, r0 = (item % groups) * 2 * PAIRS;
+    cp_async_wait<1>();
+    __syncthreads();
+    float2 res[A];
+    if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
+      const float2* in = reinterpret_cast<const float2*>(stg + stage * stage_bytes);
+      float2 v[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int n = a1 + A * b;
+        const int m = n <= H ? n : L - n;
+        float2 ya = in[(2 * line1) * NPp + m];
+        float2 yb = in[(2 * line1 + 1) * NPp + m];
+        if (n > H) {
+          ya = cconj(ya);
+          yb = cconj(yb);
+        }
+        v[b] = make_float2(ya.x - yb.y, ya.y + yb.x);
+      }
+      Dft<B, 1>::run(v);
+#pragma unroll
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a1]);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) sm[line1 * LS + kb * (A + 1) + a1] = v[kb];
+      __syncthreads();
+      if constexpr (MODE == ROW_C2R) issue(item + 2 * gridDim.x, stage);
+      const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
+      if (in2) {
+#pragma unroll
+        for (int aa = 0; aa < A; ++aa) res[aa] = sm[line2 * LS + kb2 * (A + 1) + aa];
+        Dft<A, 1>::run(res);
+#pragma unroll
+        for (int ka = 0; ka < A; ++ka) {
+          float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
+          if (p.use_thr) {
+            if (fabsf(c0) < thr) c0 = 0.f;
+            if (fabsf(c1) < thr) c1 = 0.f;
+          }
+          res[ka] = make_float2(c0, c1);
+        }
+      }
+      if constexpr (MODE == ROW_C2R) {
+        if (in2) {
+          float* o0 = p.out_real + (int64_t)slot * p.out_stride + (int64_t)(r0 + 2 * line2) * L;
+#pragma unroll
+          for (int ka = 0; ka < A; ++ka) {
+            const int kk = kb2 + B * ka;
+            o0[kk] = res[ka].x;
+            o0[L + kk] = res[ka].y;
+          }
+        }
+        __syncthreads();  // exchange reused by the next item
+        continue;
+      }
+      __syncthreads();
+      if (in2) {
+#pragma unroll
+        for (int ka = 0; ka < A; ++ka) sm[line2 * L + kb2 + B * ka] = res[ka];
+      }
+      __syncthreads();
+    }
+    // real rows -> half spectra
+    {
+      float2 v[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int n = a1 + A * b;
+        if constexpr (MODE == ROW_R2C) {
+          const float* in = reinterpret_cast<const float*>(stg + stage * stage_bytes);
+          v[b] = make_float2(in[(2 * line1) * L + n], in[(2 * line1 + 1) * L + n]);
+        } else {
+          v[b] = sm[line1 * L + n];
+        }
+      }
+      __syncthreads();  // stage (R2C) or natural rows (RT) consumed
+      issue(item + 2 * gridDim.x, stage);
+      Dft<B, -1>::run(v);
+#pragma unroll
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a1]);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) sm[line1 * LS + kb * (A + 1) + a1] = v[kb];
+    }
+    __syncthreads();
+    if (in2) {
+#pragma unroll
+      for (int aa = 0; aa < A; ++aa) res[aa] = sm[line2 * LS + kb2 * (A + 1) + aa];
+      Dft<A, -1>::run(res);
+    }
+    __syncthreads();
+    if (in2) {
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) sm[line2 * L + kb2 + B * ka] = res[ka];
+    }
+    __syncthreads();
+    float2* out = p.out_half + (int64_t)slot * p.out_stride;
+    constexpr int HP = H + 1;
+    for (int it = tid; it < PAIRS * HP; it += T) {
+      const int line = it / HP, kk = it % HP;
+      const float2 z = sm[line * L + kk];
+      const float2 w = sm[line * L + ((L - kk) & (L - 1))];
+      out[tm.at(r0 + 2 * line, kk)] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
+      out[tm.at(r0 + 2 * line + 1, kk)] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+    }
+    __syncthreads();  // exchange reused by the next item
+  }
+  cp_async_wait<0>();
+}
+
+// Inverse filter pass (COL_INV_ACC) as a persistent pipelined kernel: work item i is
+// (tile i % ntiles, split i / ntiles); the CTA streams the (Z_j tile, psi_j tile)
+// pairs of its items' filters through two shared-memory stages and accumulates
+// psi_j * FFT_0(Z_j) in registers, writing one partial per item.
 template <int L>
-constexpr int row_smem_bytes() {
-  return (kThreads / Split<L>::B) * Split<L>::B * (Split<L>::A + 1) * (int)sizeof(float2);
+__global__ void __launch_bounds__(Geo<L>::T) k_col_inv_pipe(ColArgs p) {
+  using G = Geo<L>;
+  constexpr int A = G::A, B = G::B, TC = G::TC, T = G::T, XS = G::XS;
+  constexpr int TILE = L * TC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* zs = reinterpret_cast<float2*>(smraw);        // [2][TILE]
+  float* ps = reinterpret_cast<float*>(zs + 2 * TILE);  // [2][TILE]
+  float2* ex = reinterpret_cast<float2*>(ps + 2 * TILE);
+  const int tid = threadIdx.x;
+  const float2* tw = g_twiddle + twiddle_offset(L);
+  const int ntiles = (int)(p.Nhp / TILE);
+  const int nsplit = (p.nfilt + p.fps - 1) / p.fps;
+  const int nitems = ntiles * nsplit;
+  const int line = tid % TC, a = tid / TC;
+  const int line2 = tid % TC, kb2 = tid / TC;
+  const bool in2 = tid < TC * B;
+
+  // the CTA's load sequence: (item, filter) pairs in order
+  auto first_filter = [&](int item) { return (item / ntiles) * p.fps; };
+  auto last_filter = [&](int item) { return min(first_filter(item) + p.fps, p.nfilt); };
+  auto issue = [&](int item, int f, int stage) {
+    if (item < nitems) {
+      const int tile = item % ntiles;
+      cp_async_block<T>(zs + stage * TILE, p.in + (int64_t)f * p.Nhp + (int64_t)tile * TILE, TILE * 8);
+      cp_async_block<T>(ps + stage * TILE, p.psi + (int64_t)(p.j0 + f) * p.Nhp + (int64_t)tile * TILE,
+                        TILE * 4);
+    }
+    cp_async_commit();
+  };
+  auto advance = [&](int& item, int& f) {
+    if (++f >= last_filter(item)) {
+      item += gridDim.x;
+      f = item < nitems ? first_filter(item) : 0;
+    }
+  };
+
+  int cur_item = blockIdx.x, cur_f = cur_item < nitems ? first_filter(cur_item) : 0;
+  int pre_item = cur_item, pre_f = cur_f;  // next load to issue
+  issue(pre_item, pre_f, 0);
+  advance(pre_item, pre_f);
+  issue(pre_item, pre_f, 1);
+  advance(pre_item, pre_f);
+  float2 acc[A];
+#pragma unroll
+  for (int i = 0; i < A; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int k = 0; cur_item < nitems; ++k) {
+    const int stage = k & 1;
+    cp_async_wait<1>();
+    __syncthreads();
+    float2 v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = zs[stage * TILE + (a + A * b) * TC + line];
+    Dft<B, -1>::run(v);
+#pragma unroll
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a]);
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) ex[kb * XS + a * TC + line] = v[kb];
+    __syncthreads();
+    if (in2) {
+      float2 w[A];
+#pragma unroll
+      for (int aa = 0; aa < A; ++aa) w[aa] = ex[kb2 * XS + aa * TC + line2];
+      Dft<A, -1>::run(w);
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) {
+        const float f = ps[stage * TILE + (kb2 + B * ka) * TC + line2];
+        acc[ka].x = fmaf(f, w[ka].x, acc[ka].x);
+        acc[ka].y = fmaf(f, w[ka].y, acc[ka].y);
+      }
+    }
+    __syncthreads();  // stage and exchange consumed
+    issue(pre_item, pre_f, stage);
+    advance(pre_item, pre_f);
+    const int done_item = cur_item;
+    advance(cur_item, cur_f);
+    if (cur_item != done_item) {  // item complete: write its partial
+      if (in2) {
+        const int tile = done_item % ntiles, split = done_item / ntiles;
+        float2* o = p.out + (int64_t)(p.part0 + split) * p.Nhp + (int64_t)tile * TILE;
+#pragma unroll
+        for (int ka = 0; ka < A; ++ka) {
+          o[(kb2 + B * ka) * TC + line2] = acc[ka];
+          acc[ka] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int L>
+constexpr int col_inv_pipe_smem_bytes() {
+  return 2 * L * Geo<L>::TC * (8 + 4) + Geo<L>::B * Geo<L>::XS * 8;
 }
 
 // ------------------------------------------------------------ elementwise ---
 
 // In-place hard threshold of nf consecutive coefficient arrays of n elements each.
-__global__ void __launch_bounds__(kThreads) k_threshold(float* c, int64_t n, int nf,
-                                                        Thresholds thr) {
+__global__ void __launch_bounds__(256) k_threshold(float* c, int64_t n, int nf, Thresholds thr) {
   const int f = blockIdx.y;
   if (f >= nf) return;
   const float t = thr.v[f];

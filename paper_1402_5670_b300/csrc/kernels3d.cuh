@@ -54,8 +54,9 @@ __device__ __forceinline__ void plane_col_fft(const float2* src, float2* wk, flo
 //   ROW_C2R  half-spectrum plane -> real plane * scale (optional threshold)
 //   ROW_R2C  real plane -> half-spectrum plane
 //   ROW_RT   half -> real * scale -> threshold -> half
-// in/out slot strides are in elements of their own type; one plane of a slot starts
-// at i0 * (L1 * NH) (half) or i0 * (L1 * L2) (real).
+// in/out slot strides are in elements of their own type. Spectra are tile-major
+// (p.tm): point p = k1 * NH + k2 of plane i0 lives at p.tm.at(i0, p); real planes are
+// row-major and plane i0 starts at i0 * (L1 * L2).
 template <int L1, int L2, int MODE>
 __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
   using G = PlaneGeom<L1, L2>;
@@ -72,8 +73,8 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
   const float2* tw = g_twiddle + twiddle_offset(L2);
 
   if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
-    const float2* in = p.in_half + (int64_t)slot * p.in_stride + (int64_t)i0 * G::HALF;
-    for (int i = tid; i < G::HALF; i += kPlaneThreads) P[i] = in[i];
+    const float2* in = p.in_half + (int64_t)slot * p.in_stride;
+    for (int i = tid; i < G::HALF; i += kPlaneThreads) P[i] = in[p.tm.at(i0, i)];
     __syncthreads();
     plane_col_fft<L1, NH, 1>(P, W, P);
     // rows (2q, 2q+1): complex inverse DFT of the Hermitian-extended pair
@@ -172,8 +173,8 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
     }
     __syncthreads();
     plane_col_fft<L1, NH, -1>(W, P, W);
-    float2* out = p.out_half + (int64_t)slot * p.out_stride + (int64_t)i0 * G::HALF;
-    for (int i = tid; i < G::HALF; i += kPlaneThreads) out[i] = W[i];
+    float2* out = p.out_half + (int64_t)slot * p.out_stride;
+    for (int i = tid; i < G::HALF; i += kPlaneThreads) out[p.tm.at(i0, i)] = W[i];
   }
 }
 

@@ -13,18 +13,20 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/shearlet.h"
 #include "bank_host.h"
 #include "kernels3d.cuh"
+#include "kernels_cluster.cuh"
 
 using sl::dev::ColArgs;
 using sl::dev::RowArgs;
 using sl::dev::Thresholds;
 using sl::dev::kMaxGroup;
-using sl::dev::kThreads;
 using sl::dev::kPlaneThreads;
+using sl::dev::TileMap;
 
 // ------------------------------------------------------------------ errors ---
 
@@ -133,12 +135,13 @@ static cudaError_t ensure_smem(K kernel, int bytes) {
 template <int L, int MODE>
 static cudaError_t launch_col_t(dim3 grid, cudaStream_t st, const ColArgs& a) {
   auto k = sl::dev::k_col<L, MODE>;
-  constexpr int smem = sl::dev::col_smem_bytes<L>();
+  constexpr int smem = sl::dev::Geo<L>::smem_col;
   cudaError_t e = ensure_smem(k, smem);
   if (e != cudaSuccess) return e;
   static const char* names[4] = {"col_spec", "col_fwd_filter", "col_inv_accumulate",
-                                 "col_inv_final"};
-  return timed_launch(names[MODE], st, [&]() { k<<<grid, kThreads, smem, st>>>(a); });
+                                 "col_ifft"};
+  return timed_launch(names[MODE], st,
+                      [&]() { k<<<grid, sl::dev::Geo<L>::T, smem, st>>>(a); });
 }
 
 template <int MODE>
@@ -156,46 +159,159 @@ static cudaError_t launch_col(int L, dim3 grid, cudaStream_t st, const ColArgs& 
   }
 }
 
-static int col_tile(int L) {  // pencils per CTA = 256 / B
-  switch (L) {
-    case 8: return 128;
-    case 16: return 64;
-    case 32: return 64;
-    case 64: return 32;
-    case 128: return 32;
-    case 256: return 16;
-    case 512: return 16;
-    default: return 8;
+static int col_tile(int L) { return sl::dev::col_tile_of(L); }  // pencils per CTA
+
+// Persistent pipelined forward filter pass: as many CTAs as fit on the device.
+template <int L>
+static cudaError_t launch_col_fwd_pipe_t(int nitems, cudaStream_t st, const ColArgs& a) {
+  auto k = sl::dev::k_col_fwd_pipe<L>;
+  constexpr int smem = sl::dev::col_pipe_smem_bytes<L>();
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  static int per_sm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && per_sm[dev] == 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, sl::dev::Geo<L>::T, smem) != cudaSuccess)
+      n = 1;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    per_sm[dev] = std::max(1, n) * sms;
   }
+  const int grid = std::min(nitems, per_sm[(dev >= 0 && dev < 64) ? dev : 0]);
+  return timed_launch("col_fwd_filter", st,
+                      [&]() { k<<<grid, sl::dev::Geo<L>::T, smem, st>>>(a); });
+}
+
+// CTAs of a persistent kernel: the device's SMs times the CTAs that fit on one.
+template <typename K>
+static int persistent_grid(K kernel, int threads, int smem, int kernel_id) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> cache;  // (device, kernel, smem)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({dev, kernel_id, smem});
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int g = std::max(1, n) * sms;
+  cache[{dev, kernel_id, smem}] = g;
+  return g;
 }
 
 template <int L, int MODE>
-static cudaError_t launch_row_t(dim3 grid, cudaStream_t st, const RowArgs& a) {
-  auto k = sl::dev::k_row<L, MODE>;
-  constexpr int smem = sl::dev::row_smem_bytes<L>();
-  cudaError_t e = ensure_smem(k, smem);
+static cudaError_t launch_row_pipe_t(int slots, int L0, int NPp, cudaStream_t st,
+                                     const RowArgs& a) {
+  constexpr int PAIRS = sl::dev::col_tile_of(L);
+  constexpr int T = PAIRS * sl::dev::Split<L>::A;
+  auto k = sl::dev::k_row_pipe<L, MODE, PAIRS>;
+  const int stage = MODE == sl::dev::ROW_R2C ? 2 * PAIRS * L * 4 : 2 * PAIRS * NPp * 8;
+  const int smem = 2 * stage + sl::dev::RowPipe<L, MODE, PAIRS>::XB;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  const int items = slots * (L0 / (2 * PAIRS));
+  const int grid = std::min(items, persistent_grid(k, T, smem, 1000 * L + MODE));
   static const char* names[3] = {"row_r2c", "row_c2r", "row_roundtrip"};
-  return timed_launch(names[MODE], st, [&]() { k<<<grid, kThreads, smem, st>>>(a); });
+  return timed_launch(names[MODE], st,
+                      [&]() { k<<<grid, T, smem, st>>>(a, slots, NPp, stage); });
 }
 
 template <int MODE>
-static cudaError_t launch_row(int L, dim3 grid, cudaStream_t st, const RowArgs& a) {
+static cudaError_t launch_row_pipe(int L, int slots, int L0, int NPp, cudaStream_t st,
+                                   const RowArgs& a) {
   switch (L) {
-    case 8: return launch_row_t<8, MODE>(grid, st, a);
-    case 16: return launch_row_t<16, MODE>(grid, st, a);
-    case 32: return launch_row_t<32, MODE>(grid, st, a);
-    case 64: return launch_row_t<64, MODE>(grid, st, a);
-    case 128: return launch_row_t<128, MODE>(grid, st, a);
-    case 256: return launch_row_t<256, MODE>(grid, st, a);
-    case 512: return launch_row_t<512, MODE>(grid, st, a);
-    case 1024: return launch_row_t<1024, MODE>(grid, st, a);
+    case 8: return launch_row_pipe_t<8, MODE>(slots, L0, NPp, st, a);
+    case 16: return launch_row_pipe_t<16, MODE>(slots, L0, NPp, st, a);
+    case 32: return launch_row_pipe_t<32, MODE>(slots, L0, NPp, st, a);
+    case 64: return launch_row_pipe_t<64, MODE>(slots, L0, NPp, st, a);
+    case 128: return launch_row_pipe_t<128, MODE>(slots, L0, NPp, st, a);
+    case 256: return launch_row_pipe_t<256, MODE>(slots, L0, NPp, st, a);
+    case 512: return launch_row_pipe_t<512, MODE>(slots, L0, NPp, st, a);
+    case 1024: return launch_row_pipe_t<1024, MODE>(slots, L0, NPp, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
 
-static int row_pairs_per_cta(int L) {  // 256 / B
-  return col_tile(L);
+template <int L>
+static cudaError_t launch_col_inv_pipe_t(int nitems, cudaStream_t st, const ColArgs& a) {
+  auto k = sl::dev::k_col_inv_pipe<L>;
+  constexpr int smem = sl::dev::col_inv_pipe_smem_bytes<L>();
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(nitems, persistent_grid(k, sl::dev::Geo<L>::T, smem, 2000 + L));
+  return timed_launch("col_inv_accumulate", st,
+                      [&]() { k<<<grid, sl::dev::Geo<L>::T, smem, st>>>(a); });
+}
+
+static cudaError_t launch_col_inv_pipe(int L, int nitems, cudaStream_t st, const ColArgs& a) {
+  switch (L) {
+    case 8: return launch_col_inv_pipe_t<8>(nitems, st, a);
+    case 16: return launch_col_inv_pipe_t<16>(nitems, st, a);
+    case 32: return launch_col_inv_pipe_t<32>(nitems, st, a);
+    case 64: return launch_col_inv_pipe_t<64>(nitems, st, a);
+    case 128: return launch_col_inv_pipe_t<128>(nitems, st, a);
+    case 256: return launch_col_inv_pipe_t<256>(nitems, st, a);
+    case 512: return launch_col_inv_pipe_t<512>(nitems, st, a);
+    case 1024: return launch_col_inv_pipe_t<1024>(nitems, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t launch_col_fwd_pipe(int L, int nitems, cudaStream_t st, const ColArgs& a) {
+  switch (L) {
+    case 8: return launch_col_fwd_pipe_t<8>(nitems, st, a);
+    case 16: return launch_col_fwd_pipe_t<16>(nitems, st, a);
+    case 32: return launch_col_fwd_pipe_t<32>(nitems, st, a);
+    case 64: return launch_col_fwd_pipe_t<64>(nitems, st, a);
+    case 128: return launch_col_fwd_pipe_t<128>(nitems, st, a);
+    case 256: return launch_col_fwd_pipe_t<256>(nitems, st, a);
+    case 512: return launch_col_fwd_pipe_t<512>(nitems, st, a);
+    case 1024: return launch_col_fwd_pipe_t<1024>(nitems, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Row passes: PAIRS row pairs per CTA. Launches over many filters use the wide
+// variant (col_tile_of(L) pairs); single-image launches use one pair per CTA so that
+// the few rows of one image still spread over many SMs.
+template <int L, int MODE, int PAIRS>
+static cudaError_t launch_row_p(dim3 grid, cudaStream_t st, const RowArgs& a) {
+  auto k = sl::dev::k_row<L, MODE, PAIRS>;
+  constexpr int A = sl::dev::Split<L>::A, B = sl::dev::Split<L>::B;
+  constexpr int smem = PAIRS * B * (A + 1) * (int)sizeof(float2);
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  static const char* names[3] = {"row_r2c", "row_c2r", "row_roundtrip"};
+  return timed_launch(names[MODE], st, [&]() { k<<<grid, PAIRS * A, smem, st>>>(a); });
+}
+
+template <int L, int MODE>
+static cudaError_t launch_row_t(int slots, int L0, cudaStream_t st, const RowArgs& a) {
+  constexpr int W = sl::dev::col_tile_of(L);
+  if (slots == 1) return launch_row_p<L, MODE, 1>(dim3(L0 / 2, 1), st, a);
+  return launch_row_p<L, MODE, W>(dim3((L0 / 2 + W - 1) / W, slots), st, a);
+}
+
+template <int MODE>
+static cudaError_t launch_row(int L, int slots, int L0, cudaStream_t st, const RowArgs& a) {
+  switch (L) {
+    case 8: return launch_row_t<8, MODE>(slots, L0, st, a);
+    case 16: return launch_row_t<16, MODE>(slots, L0, st, a);
+    case 32: return launch_row_t<32, MODE>(slots, L0, st, a);
+    case 64: return launch_row_t<64, MODE>(slots, L0, st, a);
+    case 128: return launch_row_t<128, MODE>(slots, L0, st, a);
+    case 256: return launch_row_t<256, MODE>(slots, L0, st, a);
+    case 512: return launch_row_t<512, MODE>(slots, L0, st, a);
+    case 1024: return launch_row_t<1024, MODE>(slots, L0, st, a);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int L1, int L2, int MODE>
@@ -232,6 +348,82 @@ static cudaError_t launch_plane(int L1, int L2, dim3 grid, cudaStream_t st, cons
   }
 }
 
+// ------------------------------------------------------- cluster-fused 2D ---
+
+using sl::dev::ClArgs;
+using sl::dev::ClGeo;
+
+template <int L0, int L1>
+static cudaError_t cl_fwd_launch(int ncl, cudaStream_t st, const ClArgs& a) {
+  auto k = sl::dev::k_cl_fwd<L0, L1>;
+  constexpr int smem = ClGeo<L0, L1>::smem;
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  return timed_launch(a.psi ? "cluster_fwd_filters" : "cluster_c2r", st, [&]() {
+    k<<<ncl * sl::dev::kCluster, ClGeo<L0, L1>::NT, smem, st>>>(a);
+  });
+}
+
+template <int L0, int L1>
+static cudaError_t cl_inv_launch(int ncl, cudaStream_t st, const ClArgs& a) {
+  auto k = sl::dev::k_cl_inv<L0, L1>;
+  constexpr int smem = ClGeo<L0, L1>::smem;
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  return timed_launch(a.psi ? "cluster_inv_filters" : "cluster_r2c", st, [&]() {
+    k<<<ncl * sl::dev::kCluster, ClGeo<L0, L1>::NT, smem, st>>>(a);
+  });
+}
+
+// How many 8-CTA clusters of this kernel can be resident at once.
+template <int L0, int L1>
+static int cl_max_clusters() {
+  int best = 1 << 30;
+  for (int which = 0; which < 2; ++which) {
+    const void* k = which ? (const void*)sl::dev::k_cl_inv<L0, L1>
+                          : (const void*)sl::dev::k_cl_fwd<L0, L1>;
+    constexpr int smem = ClGeo<L0, L1>::smem;
+    if (which) ensure_smem(sl::dev::k_cl_inv<L0, L1>, smem);
+    else ensure_smem(sl::dev::k_cl_fwd<L0, L1>, smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sl::dev::kCluster * 64, 1, 1);
+    cfg.blockDim = dim3(ClGeo<L0, L1>::NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    best = std::min(best, n);
+  }
+  return best;
+}
+
+struct ClEntry {
+  int L0, L1;
+  cudaError_t (*fwd)(int, cudaStream_t, const ClArgs&);
+  cudaError_t (*inv)(int, cudaStream_t, const ClArgs&);
+  int (*max_clusters)();
+  int CW, TOTAL;
+};
+
+#define SL_CL(a, b) \
+  {a, b, &cl_fwd_launch<a, b>, &cl_inv_launch<a, b>, &cl_max_clusters<a, b>, ClGeo<a, b>::CW, ClGeo<a, b>::TOTAL}
+static const ClEntry kClTable[] = {
+    SL_CL(64, 64),   SL_CL(64, 128),  SL_CL(64, 256),  SL_CL(64, 512),
+    SL_CL(128, 64),  SL_CL(128, 128), SL_CL(128, 256), SL_CL(128, 512),
+    SL_CL(256, 64),  SL_CL(256, 128), SL_CL(256, 256), SL_CL(256, 512),
+    SL_CL(512, 64),  SL_CL(512, 128), SL_CL(512, 256), SL_CL(512, 512),
+};
+#undef SL_CL
+
+static const ClEntry* cl_entry(const sl::BankSpec& s) {
+  if (s.ndim != 2) return nullptr;
+  for (const ClEntry& e : kClTable)
+    if (e.L0 == s.dims[0] && e.L1 == s.dims[1]) return &e;
+  return nullptr;
+}
+
 // ------------------------------------------------------------------- bank ---
 
 struct sl_bank {
@@ -242,15 +434,25 @@ struct sl_bank {
   int device = -1;
   int R = 0;
   int64_t N = 0, Nh = 0;
+  int NP = 0;       // pencils per spectrum (Nh / n0)
+  int TC = 1, lgTC = 0, ntiles = 0;
+  int64_t Nhp = 0;  // elements of one tile-major (padded) spectrum
   int G = 1;        // filters per group
   int ngroups = 1;
   int S = 1;        // partials per group
   int fps = 1;      // filters per partial
-  float* psi = nullptr;       // [R][Nh]
-  double* invPsi = nullptr;   // [Nh]
-  float2* xhat = nullptr;     // [Nh] spectrum of the signal
-  float2* scratch = nullptr;  // [G][Nh]
-  float2* partial = nullptr;  // [ngroups * S][Nh]
+  float* psi = nullptr;       // [R][Nhp] tile-major
+  double* invPsi = nullptr;   // [Nhp] tile-major
+  float2* xhat = nullptr;     // [Nhp] spectrum of the signal
+  float2* scratch = nullptr;  // [G][Nhp]
+  float2* partial = nullptr;  // [ngroups * S][Nhp]
+  // cluster-fused 2D path (cl != nullptr): cluster-tiled filters and spectra
+  const ClEntry* cl = nullptr;
+  int ncl = 0;                // clusters of the filter passes
+  float* psi_cl = nullptr;    // [R][TOTAL]
+  double* invPsi_cl = nullptr;
+  float2* xhat_cl = nullptr;  // [TOTAL]
+  float2* part_cl = nullptr;  // [ncl][TOTAL]
   float* e2e_x = nullptr;     // sl_fwdinv_host buffers (allocated on first use)
   float* e2e_c = nullptr;
   std::unique_ptr<sl::BankEvaluator> ev;
@@ -266,6 +468,13 @@ static void free_device(sl_bank* b) {
   cudaFree(b->partial);
   cudaFree(b->e2e_x);
   cudaFree(b->e2e_c);
+  cudaFree(b->psi_cl);
+  cudaFree(b->invPsi_cl);
+  cudaFree(b->xhat_cl);
+  cudaFree(b->part_cl);
+  b->psi_cl = nullptr;
+  b->invPsi_cl = nullptr;
+  b->xhat_cl = b->part_cl = nullptr;
   b->psi = nullptr;
   b->invPsi = nullptr;
   b->xhat = b->scratch = b->partial = nullptr;
@@ -278,19 +487,37 @@ static void free_device(sl_bank* b) {
 static void plan_groups(sl_bank* b) {
   double mb = 48.0;
   if (const char* s = std::getenv("SL_SCRATCH_MB")) mb = std::max(1.0, std::atof(s));
-  const double per = (double)b->Nh * sizeof(float2);
+  const double per = (double)b->Nhp * sizeof(float2);
   int gmax = (int)std::max(1.0, std::floor(mb * 1024.0 * 1024.0 / per));
   gmax = std::min(gmax, kMaxGroup);
   b->ngroups = (b->R + gmax - 1) / gmax;
   b->G = (b->R + b->ngroups - 1) / b->ngroups;
-  // pencil tiles of the inverse accumulation; split filters so that the grid covers
-  // the GPU about twice (148 SMs on B300), with at least 2 filters per split.
-  const int L0 = (int)b->spec.dims[0];
-  const int NP = (int)(b->Nh / L0);
-  const int tiles = (NP + col_tile(L0) - 1) / col_tile(L0);
-  int want = std::max(1, (2 * 148 + tiles - 1) / tiles);
+  // pencil tiles of the inverse accumulation; split filters so that the grid holds
+  // about four small CTAs per SM (148 SMs on B300), with at least 2 filters per split.
+  const int tiles = b->ntiles;
+  int want = std::max(1, (4 * 148 + tiles - 1) / tiles);
   b->fps = std::max(2, (b->G + want - 1) / want);
   b->S = (b->G + b->fps - 1) / b->fps;
+}
+
+// Natural half spectrum [n0][NP] -> tile-major [ntiles][n0][TC] (pads untouched).
+template <typename T>
+static void tile_major(const sl_bank* b, const T* nat, T* tiled) {
+  const int L0 = (int)b->spec.dims[0];
+  for (int k0 = 0; k0 < L0; ++k0)
+    for (int p = 0; p < b->NP; ++p)
+      tiled[(((int64_t)(p >> b->lgTC) * L0 + k0) << b->lgTC) + (p & (b->TC - 1))] =
+          nat[(int64_t)k0 * b->NP + p];
+}
+
+// Natural half spectrum [n0][NH] -> cluster-tiled [8][n0][CW] (pads untouched).
+template <typename T>
+static void cluster_tiled(const sl_bank* b, const T* nat, T* ct) {
+  const int L0 = (int)b->spec.dims[0];
+  const int NH = (int)b->NP, CW = b->cl->CW;
+  for (int k0 = 0; k0 < L0; ++k0)
+    for (int c = 0; c < NH; ++c)
+      ct[(int64_t)(c / CW) * L0 * CW + (int64_t)k0 * CW + c % CW] = nat[(int64_t)k0 * NH + c];
 }
 
 extern "C" {
@@ -312,8 +539,15 @@ const char* sl_last_error(void) { return g_last_error.c_str(); }
 
 sl_status sl_build_filters(int ndim, const int64_t* dims, int nScales, const int* shearLevels,
                            int fullSystem, int device, sl_bank** out) {
+  return sl_build_filters_ex(ndim, dims, nScales, shearLevels, fullSystem, device, nullptr, out);
+}
+
+sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const int* shearLevels,
+                              int fullSystem, int device, const sl_options* opt, sl_bank** out) {
   if (!out) return fail(SL_EINVAL, "out is NULL");
   *out = nullptr;
+  const int path = opt ? opt->path : SL_PATH_AUTO;
+  if (path < SL_PATH_AUTO || path > SL_PATH_CLUSTER) return fail(SL_EINVAL, "unknown path");
   if (ndim != 2 && ndim != 3) return fail(SL_EINVAL, "ndim must be 2 or 3");
   if (!dims || !shearLevels) return fail(SL_EINVAL, "dims or shearLevels is NULL");
   if (nScales < 1 || nScales > 8) return fail(SL_EINVAL, "nScales must be in [1, 8]");
@@ -343,6 +577,11 @@ sl_status sl_build_filters(int ndim, const int64_t* dims, int nScales, const int
   b->device = device;
   b->N = N;
   b->Nh = Nh;
+  b->NP = (int)(Nh / spec.dims[0]);
+  b->TC = col_tile((int)spec.dims[0]);
+  while ((1 << b->lgTC) < b->TC) ++b->lgTC;
+  b->ntiles = (b->NP + b->TC - 1) / b->TC;
+  b->Nhp = spec.dims[0] * (int64_t)b->ntiles * b->TC;
 
   sl::HostBank hb;
   std::string err;
@@ -366,23 +605,83 @@ sl_status sl_build_filters(int ndim, const int64_t* dims, int nScales, const int
     auto alloc = [&](void** p, size_t bytes) -> bool {
       return cudaMalloc(p, bytes) == cudaSuccess;
     };
-    if (!alloc((void**)&b->psi, (size_t)b->R * Nh * sizeof(float)) ||
-        !alloc((void**)&b->invPsi, (size_t)Nh * sizeof(double)) ||
-        !alloc((void**)&b->xhat, (size_t)Nh * sizeof(float2)) ||
-        !alloc((void**)&b->scratch, (size_t)b->G * Nh * sizeof(float2)) ||
-        !alloc((void**)&b->partial, (size_t)b->ngroups * b->S * Nh * sizeof(float2))) {
+    const int64_t Nhp = b->Nhp;
+    if (!alloc((void**)&b->psi, (size_t)b->R * Nhp * sizeof(float)) ||
+        !alloc((void**)&b->invPsi, (size_t)Nhp * sizeof(double)) ||
+        !alloc((void**)&b->xhat, (size_t)Nhp * sizeof(float2)) ||
+        !alloc((void**)&b->scratch, (size_t)b->G * Nhp * sizeof(float2)) ||
+        !alloc((void**)&b->partial, (size_t)b->ngroups * b->S * Nhp * sizeof(float2))) {
       cudaGetLastError();
       free_device(b.get());
       return fail(SL_ENOMEM, "device allocation failed");
     }
-    cudaError_t e = cudaMemcpy(b->psi, hb.psi32.data(), (size_t)b->R * Nh * sizeof(float),
-                               cudaMemcpyHostToDevice);
+    // the spectra's pad pencils must hold zeros (see kernels2d.cuh)
+    cudaError_t e = cudaMemset(b->xhat, 0, (size_t)Nhp * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(b->scratch, 0, (size_t)b->G * Nhp * sizeof(float2));
     if (e == cudaSuccess)
-      e = cudaMemcpy(b->invPsi, hb.invPsi.data(), (size_t)Nh * sizeof(double),
-                     cudaMemcpyHostToDevice);
+      e = cudaMemset(b->partial, 0, (size_t)b->ngroups * b->S * Nhp * sizeof(float2));
+    // filters and 1/Psi in the tile-major layout, zeros in the pads
+    {
+      std::vector<float> tiled((size_t)Nhp, 0.0f);
+      for (int j = 0; j < b->R && e == cudaSuccess; ++j) {
+        tile_major(b.get(), hb.psi32.data() + (size_t)j * Nh, tiled.data());
+        e = cudaMemcpy(b->psi + (size_t)j * Nhp, tiled.data(), (size_t)Nhp * sizeof(float),
+                       cudaMemcpyHostToDevice);
+      }
+      std::vector<double> ip((size_t)Nhp, 0.0);
+      tile_major(b.get(), hb.invPsi.data(), ip.data());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(b->invPsi, ip.data(), (size_t)Nhp * sizeof(double),
+                       cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
       free_device(b.get());
       return cuda_fail(e, "uploading the filter bank");
+    }
+    // cluster-fused 2D path
+    const ClEntry* ce = cl_entry(spec);
+    if (path == SL_PATH_CLUSTER && !ce) {
+      free_device(b.get());
+      return fail(SL_ENOTSUP, "the cluster path covers 2D grids with both sides in [64, 512]");
+    }
+    // SL_PATH_AUTO takes the general path: on B300 it measures faster than the
+    // cluster-fused kernels for every size the cluster path covers.
+    if (path == SL_PATH_CLUSTER && ce) {
+      const int maxcl = ce->max_clusters();
+      if (maxcl < 1) {
+        if (path == SL_PATH_CLUSTER) {
+          free_device(b.get());
+          return fail(SL_ENOTSUP, "no 8-CTA cluster of the fused kernels fits on this device");
+        }
+      } else {
+        b->cl = ce;
+        b->ncl = std::min(maxcl, b->R);
+        const int64_t T = ce->TOTAL;
+        if (!alloc((void**)&b->psi_cl, (size_t)b->R * T * sizeof(float)) ||
+            !alloc((void**)&b->invPsi_cl, (size_t)T * sizeof(double)) ||
+            !alloc((void**)&b->xhat_cl, (size_t)T * sizeof(float2)) ||
+            !alloc((void**)&b->part_cl, (size_t)b->ncl * T * sizeof(float2))) {
+          cudaGetLastError();
+          free_device(b.get());
+          return fail(SL_ENOMEM, "device allocation failed (cluster path)");
+        }
+        std::vector<float> ct((size_t)T, 0.0f);
+        for (int j = 0; j < b->R && e == cudaSuccess; ++j) {
+          cluster_tiled(b.get(), hb.psi32.data() + (size_t)j * Nh, ct.data());
+          e = cudaMemcpy(b->psi_cl + (size_t)j * T, ct.data(), (size_t)T * sizeof(float),
+                         cudaMemcpyHostToDevice);
+        }
+        std::vector<double> ip((size_t)T, 0.0);
+        cluster_tiled(b.get(), hb.invPsi.data(), ip.data());
+        if (e == cudaSuccess)
+          e = cudaMemcpy(b->invPsi_cl, ip.data(), (size_t)T * sizeof(double),
+                         cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(b->xhat_cl, 0, (size_t)T * sizeof(float2));
+        if (e != cudaSuccess) {
+          free_device(b.get());
+          return cuda_fail(e, "uploading the cluster-tiled filter bank");
+        }
+      }
     }
   }
   *out = b.release();
@@ -432,6 +731,12 @@ sl_status sl_bank_norms(const sl_bank* b, double* norms, double* A, double* B) {
   return SL_OK;
 }
 
+sl_status sl_bank_path(const sl_bank* b, int* path) {
+  if (!b || !path) return fail(SL_EINVAL, "bank or path is NULL");
+  *path = b->cl ? SL_PATH_CLUSTER : SL_PATH_GENERAL;
+  return SL_OK;
+}
+
 sl_status sl_bank_sizes(const sl_bank* b, int64_t* N, int64_t* Nh) {
   if (!b) return fail(SL_EINVAL, "bank is NULL");
   if (N) *N = b->N;
@@ -461,7 +766,17 @@ sl_status sl_bank_eval_f64(const sl_bank* b, int j, double* out) {
 sl_status sl_bank_filters_f32(const sl_bank* b, float* out) {
   if (!b || !out) return fail(SL_EINVAL, "bank or out is NULL");
   if (b->device < 0) return fail(SL_EINVAL, "host-only bank has no device filters");
-  SL_CUDA(cudaMemcpy(out, b->psi, (size_t)b->R * b->Nh * sizeof(float), cudaMemcpyDeviceToHost));
+  std::vector<float> tiled((size_t)b->Nhp);
+  for (int j = 0; j < b->R; ++j) {
+    SL_CUDA(cudaMemcpy(tiled.data(), b->psi + (size_t)j * b->Nhp, (size_t)b->Nhp * sizeof(float),
+                       cudaMemcpyDeviceToHost));
+    float* dst = out + (size_t)j * b->Nh;
+    const int L0 = (int)b->spec.dims[0];
+    for (int k0 = 0; k0 < L0; ++k0)
+      for (int pp = 0; pp < b->NP; ++pp)
+        dst[(int64_t)k0 * b->NP + pp] =
+            tiled[(((int64_t)(pp >> b->lgTC) * L0 + k0) << b->lgTC) + (pp & (b->TC - 1))];
+  }
   return SL_OK;
 }
 
@@ -489,154 +804,188 @@ static sl_status launched(cudaError_t e, const char* what) {
     if (s_ != SL_OK) return s_;       \
   } while (0)
 
-// Real signal x[dims] -> half spectrum b->xhat (rows/planes, then pencils).
-static sl_status spectrum_of(const sl_bank* b, const float* x, cudaStream_t st) {
-  const sl::BankSpec& s = b->spec;
-  const int L0 = (int)s.dims[0];
-  RowArgs ra{};
-  ra.in_real = x;
-  ra.out_half = b->xhat;
-  ra.in_stride = 0;
-  ra.out_stride = 0;
-  ra.scale = 1.f;
-  g_next_bytes = 4.0 * b->N;  // the signal is read once
-  if (s.ndim == 2) {
-    const int L1 = (int)s.dims[1];
-    ra.n_rows = L0;
-    ra.nh = (int)s.nh();
-    dim3 g((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), 1);
-    SL_TRY(launched(launch_row<sl::dev::ROW_R2C>(L1, g, st, ra), "row_r2c"));
-  } else {
-    dim3 g(L0, 1);
-    g_next_bytes = 4.0 * b->N;
-    SL_TRY(launched(launch_plane<sl::dev::ROW_R2C>((int)s.dims[1], (int)s.dims[2], g, st, ra),
-                    "plane_r2c"));
-  }
-  ColArgs ca{};
-  ca.in = b->xhat;
-  ca.out = b->xhat;
-  ca.Nh = b->Nh;
-  ca.NP = (int)(b->Nh / L0);
-  dim3 g((ca.NP + col_tile(L0) - 1) / col_tile(L0), 1);
-  return launched(launch_col<sl::dev::COL_SPEC>(L0, g, st, ca), "col_spec");
+// Everything one transform call needs: geometry, filters and the scratch spectra.
+// Built from a bank (its own scratch) or for sl_forward_noalloc (static scratch).
+struct Plan {
+  const sl::BankSpec* spec;
+  int64_t N, Nh, Nhp;
+  int NP, TC, lgTC, ntiles, R;
+  int G, ngroups, S, fps;
+  const float* psi;   // tile-major [R][Nhp], or natural [R][Nh] when psi_natural
+  int psi_natural;
+  const double* invPsi;
+  float2* xhat;       // [Nhp]
+  float2* scratch;    // [G][Nhp]
+  float2* partial;    // [ngroups * S][Nhp]
+  const sl_bank* bank;
+};
+
+static Plan plan_of(const sl_bank* b) {
+  Plan p{};
+  p.spec = &b->spec;
+  p.N = b->N;
+  p.Nh = b->Nh;
+  p.Nhp = b->Nhp;
+  p.NP = b->NP;
+  p.TC = b->TC;
+  p.lgTC = b->lgTC;
+  p.ntiles = b->ntiles;
+  p.R = b->R;
+  p.G = b->G;
+  p.ngroups = b->ngroups;
+  p.S = b->S;
+  p.fps = b->fps;
+  p.psi = b->psi;
+  p.psi_natural = 0;
+  p.invPsi = b->invPsi;
+  p.xhat = b->xhat;
+  p.scratch = b->scratch;
+  p.partial = b->partial;
+  p.bank = b;
+  return p;
 }
 
-// Per-filter "last axes" pass of one group: ROW_C2R (coeffs out), ROW_R2C (coeffs in)
-// or ROW_RT (scratch in place).
+static TileMap tilemap(const Plan& P) { return TileMap{(int)P.spec->dims[0], P.lgTC}; }
+
+// Last-axes pass (2D rows / 3D planes) over `slots` spectra.
 template <int MODE>
-static sl_status slab_pass(const sl_bank* b, int j0, int nf, const float* creal_in,
-                           float* creal_out, const Thresholds* thr, cudaStream_t st) {
-  const sl::BankSpec& s = b->spec;
+static sl_status last_axes(const Plan& P, RowArgs& ra, int slots, cudaStream_t st) {
+  const sl::BankSpec& s = *P.spec;
   const int L0 = (int)s.dims[0];
-  RowArgs ra{};
-  ra.scale = (float)(1.0 / (double)b->N);
-  ra.nh = (int)s.nh();
   ra.n_rows = L0;
+  ra.tm = tilemap(P);
+  if (s.ndim == 2) {
+    const int pairs = sl::dev::col_tile_of((int)s.dims[1]);
+    if (slots > 1 && L0 / 2 >= pairs && (L0 / 2) % pairs == 0)
+      return launched(launch_row_pipe<MODE>((int)s.dims[1], slots, L0, P.ntiles * P.TC, st, ra),
+                      "row pass");
+    return launched(launch_row<MODE>((int)s.dims[1], slots, L0, st, ra), "row pass");
+  }
+  return launched(launch_plane<MODE>((int)s.dims[1], (int)s.dims[2], dim3(L0, slots), st, ra),
+                  "plane pass");
+}
+
+// Real signal x[dims] -> spectrum P.xhat (last axes, then pencils in place).
+static sl_status spectrum_of(const Plan& P, const float* x, cudaStream_t st) {
+  RowArgs ra{};
+  ra.in_real = x;
+  ra.out_half = P.xhat;
+  ra.scale = 1.f;
+  g_next_bytes = 4.0 * P.N;  // the signal is read once
+  SL_TRY(last_axes<sl::dev::ROW_R2C>(P, ra, 1, st));
+  ColArgs ca{};
+  ca.in = P.xhat;
+  ca.out = P.xhat;
+  ca.Nhp = P.Nhp;
+  ca.NP = P.NP;
+  return launched(launch_col<sl::dev::COL_SPEC>((int)P.spec->dims[0], dim3(P.ntiles, 1), st, ca),
+                  "col_spec");
+}
+
+// Per-filter last-axes pass of one group: ROW_C2R (coefficients out), ROW_R2C
+// (coefficients in) or ROW_RT (scratch in place, thresholded).
+template <int MODE>
+static sl_status slab_pass(const Plan& P, int j0, int nf, const float* creal_in,
+                           float* creal_out, const Thresholds* thr, cudaStream_t st) {
+  RowArgs ra{};
+  ra.scale = (float)(1.0 / (double)P.N);
   if (thr) {
     ra.use_thr = 1;
     ra.thr = *thr;
   }
   if (MODE == sl::dev::ROW_C2R) {
-    ra.in_half = b->scratch;
-    ra.in_stride = b->Nh;
-    ra.out_real = creal_out + (int64_t)j0 * b->N;
-    ra.out_stride = b->N;
+    ra.in_half = P.scratch;
+    ra.in_stride = P.Nhp;
+    ra.out_real = creal_out + (int64_t)j0 * P.N;
+    ra.out_stride = P.N;
   } else if (MODE == sl::dev::ROW_R2C) {
-    ra.in_real = creal_in + (int64_t)j0 * b->N;
-    ra.in_stride = b->N;
-    ra.out_half = b->scratch;
-    ra.out_stride = b->Nh;
+    ra.in_real = creal_in + (int64_t)j0 * P.N;
+    ra.in_stride = P.N;
+    ra.out_half = P.scratch;
+    ra.out_stride = P.Nhp;
   } else {
-    ra.in_half = b->scratch;
-    ra.in_stride = b->Nh;
-    ra.out_half = b->scratch;
-    ra.out_stride = b->Nh;
+    ra.in_half = P.scratch;
+    ra.in_stride = P.Nhp;
+    ra.out_half = P.scratch;
+    ra.out_stride = P.Nhp;
   }
   // coefficients written (C2R) or read (R2C); none for the fused round trip
-  g_next_bytes = MODE == sl::dev::ROW_RT ? 0.0 : 4.0 * (double)b->N * nf;
-  if (s.ndim == 2) {
-    const int L1 = (int)s.dims[1];
-    dim3 g((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), nf);
-    return launched(launch_row<MODE>(L1, g, st, ra), "row pass");
-  }
-  g_next_bytes = MODE == sl::dev::ROW_RT ? 0.0 : 4.0 * (double)b->N * nf;
-  dim3 g(L0, nf);
-  return launched(launch_plane<MODE>((int)s.dims[1], (int)s.dims[2], g, st, ra), "plane pass");
+  g_next_bytes = MODE == sl::dev::ROW_RT ? 0.0 : 4.0 * (double)P.N * nf;
+  return last_axes<MODE>(P, ra, nf, st);
 }
 
-static sl_status fwd_filter_pass(const sl_bank* b, int j0, int nf, cudaStream_t st) {
-  const int L0 = (int)b->spec.dims[0];
+static sl_status fwd_filter_pass(const Plan& P, int j0, int nf, cudaStream_t st) {
   ColArgs ca{};
-  ca.in = b->xhat;
-  ca.out = b->scratch;
-  ca.psi = b->psi;
-  ca.Nh = b->Nh;
-  ca.NP = (int)(b->Nh / L0);
+  ca.in = P.xhat;
+  ca.out = P.scratch;
+  ca.psi = P.psi;
+  ca.psi_natural = P.psi_natural;
+  ca.Nhp = P.Nhp;
+  ca.Nh = P.Nh;
+  ca.NP = P.NP;
   ca.j0 = j0;
   ca.nfilt = nf;
-  dim3 g((ca.NP + col_tile(L0) - 1) / col_tile(L0), nf);
-  g_next_bytes = 4.0 * (double)b->Nh * nf;  // filters read
-  return launched(launch_col<sl::dev::COL_FWD_FILT>(L0, g, st, ca), "col_fwd_filter");
+  g_next_bytes = 4.0 * (double)P.Nh * nf;  // filters read
+  if (!P.psi_natural)
+    return launched(launch_col_fwd_pipe((int)P.spec->dims[0], P.ntiles * nf, st, ca),
+                    "col_fwd_filter");
+  return launched(launch_col<sl::dev::COL_FWD_FILT>((int)P.spec->dims[0], dim3(P.ntiles, nf), st,
+                                                    ca),
+                  "col_fwd_filter");
 }
 
-static sl_status inv_acc_pass(const sl_bank* b, int g_idx, int j0, int nf, cudaStream_t st) {
-  const int L0 = (int)b->spec.dims[0];
+static sl_status inv_acc_pass(const Plan& P, int g_idx, int j0, int nf, cudaStream_t st) {
   ColArgs ca{};
-  ca.in = b->scratch;
-  ca.out = b->partial;
-  ca.psi = b->psi;
-  ca.Nh = b->Nh;
-  ca.NP = (int)(b->Nh / L0);
+  ca.in = P.scratch;
+  ca.out = P.partial;
+  ca.psi = P.psi;
+  ca.Nhp = P.Nhp;
+  ca.NP = P.NP;
   ca.j0 = j0;
   ca.nfilt = nf;
-  ca.fps = b->fps;
-  ca.part0 = g_idx * b->S;
-  const int splits = (nf + b->fps - 1) / b->fps;
-  dim3 g((ca.NP + col_tile(L0) - 1) / col_tile(L0), splits);
-  g_next_bytes = 4.0 * (double)b->Nh * nf;  // filters read
-  return launched(launch_col<sl::dev::COL_INV_ACC>(L0, g, st, ca), "col_inv_accumulate");
+  ca.fps = P.fps;
+  ca.part0 = g_idx * P.S;
+  const int splits = (nf + P.fps - 1) / P.fps;
+  g_next_bytes = 4.0 * (double)P.Nh * nf;  // filters read
+  return launched(launch_col_inv_pipe((int)P.spec->dims[0], P.ntiles * splits, st, ca),
+                  "col_inv_accumulate");
 }
 
-// Partials -> spectrum (times 1/Psi for the inverse) -> real x.
-static sl_status inv_final(const sl_bank* b, int nparts_used, bool use_invpsi, float* x,
+// Partials [0, nparts) -> (sum, times 1/Psi in FP64 for the inverse) -> inverse FFT
+// along the pencils -> last axes -> real x.
+static sl_status inv_final(const Plan& P, int nparts, bool use_invpsi, float* x,
                            cudaStream_t st) {
-  const sl::BankSpec& s = b->spec;
-  const int L0 = (int)s.dims[0];
+  const int64_t n = P.Nhp;
+  const int grid = (int)std::min<int64_t>((n / 2 + 255) / 256, 4 * 148);
+  const float2* parts = P.partial;
+  const double* w = use_invpsi ? P.invPsi : nullptr;
+  float2* out = P.xhat;
+  g_next_bytes = use_invpsi ? 8.0 * (double)P.Nh : 0.0;  // 1/Psi read
+  SL_TRY(launched(timed_launch("reduce_partials", st, [&]() {
+                    sl::dev::k_reduce_parts<<<grid, 256, 0, st>>>(parts, nparts, n, w, out, n);
+                  }),
+                  "reduce_partials"));
   ColArgs ca{};
-  ca.in = b->partial;
-  ca.out = b->xhat;
-  ca.invPsi = b->invPsi;
-  ca.Nh = b->Nh;
-  ca.NP = (int)(b->Nh / L0);
-  ca.nparts = nparts_used;
-  ca.use_invpsi = use_invpsi ? 1 : 0;
-  dim3 g((ca.NP + col_tile(L0) - 1) / col_tile(L0), 1);
-  g_next_bytes = use_invpsi ? 8.0 * (double)b->Nh : 0.0;  // 1/Psi read
-  SL_TRY(launched(launch_col<sl::dev::COL_INV_FIN>(L0, g, st, ca), "col_inv_final"));
+  ca.in = P.xhat;
+  ca.out = P.xhat;
+  ca.Nhp = P.Nhp;
+  ca.NP = P.NP;
+  SL_TRY(launched(launch_col<sl::dev::COL_IFFT>((int)P.spec->dims[0], dim3(P.ntiles, 1), st, ca),
+                  "col_ifft"));
   RowArgs ra{};
-  ra.in_half = b->xhat;
+  ra.in_half = P.xhat;
   ra.out_real = x;
-  ra.scale = (float)(1.0 / (double)b->N);
-  ra.nh = (int)s.nh();
-  ra.n_rows = L0;
-  g_next_bytes = 4.0 * (double)b->N;  // the signal is written once
-  if (s.ndim == 2) {
-    const int L1 = (int)s.dims[1];
-    dim3 gr((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), 1);
-    return launched(launch_row<sl::dev::ROW_C2R>(L1, gr, st, ra), "row_c2r");
-  }
-  g_next_bytes = 4.0 * (double)b->N;
-  dim3 gp(L0, 1);
-  return launched(launch_plane<sl::dev::ROW_C2R>((int)s.dims[1], (int)s.dims[2], gp, st, ra),
-                  "plane_c2r");
+  ra.scale = (float)(1.0 / (double)P.N);
+  g_next_bytes = 4.0 * (double)P.N;  // the signal is written once
+  return last_axes<sl::dev::ROW_C2R>(P, ra, 1, st);
 }
 
 // Partials are written compactly: group g uses parts [g*S, g*S + splits_g). Every
 // group but the last holds G filters and so uses all S of its parts; the used parts
 // are therefore the contiguous range [0, parts_used).
-static int parts_used(const sl_bank* b) {
-  const int last = b->R - (b->ngroups - 1) * b->G;
-  return (b->ngroups - 1) * b->S + (last + b->fps - 1) / b->fps;
+static int parts_used(const Plan& P) {
+  const int last = P.R - (P.ngroups - 1) * P.G;
+  return (P.ngroups - 1) * P.S + (last + P.fps - 1) / P.fps;
 }
 
 static void fill_thresholds(const sl_bank* b, int j0, int nf, float sigma, const float* K,
@@ -647,15 +996,76 @@ static void fill_thresholds(const sl_bank* b, int j0, int nf, float sigma, const
   }
 }
 
-static sl_status backward(const sl_bank* b, const float* coeffs, float* x, bool use_invpsi,
-                          cudaStream_t st) {
-  for (int g = 0; g < b->ngroups; ++g) {
-    const int j0 = g * b->G;
-    const int nf = std::min(b->G, b->R - j0);
-    SL_TRY(slab_pass<sl::dev::ROW_R2C>(b, j0, nf, coeffs, nullptr, nullptr, st));
-    SL_TRY(inv_acc_pass(b, g, j0, nf, st));
+static sl_status forward_plan(const Plan& P, const float* x, float* coeffs, cudaStream_t st) {
+  SL_TRY(spectrum_of(P, x, st));
+  for (int g = 0; g < P.ngroups; ++g) {
+    const int j0 = g * P.G;
+    const int nf = std::min(P.G, P.R - j0);
+    SL_TRY(fwd_filter_pass(P, j0, nf, st));
+    SL_TRY(slab_pass<sl::dev::ROW_C2R>(P, j0, nf, nullptr, coeffs, nullptr, st));
   }
-  return inv_final(b, parts_used(b), use_invpsi, x, st);
+  return SL_OK;
+}
+
+static sl_status backward(const Plan& P, const float* coeffs, float* x, bool use_invpsi,
+                          cudaStream_t st) {
+  for (int g = 0; g < P.ngroups; ++g) {
+    const int j0 = g * P.G;
+    const int nf = std::min(P.G, P.R - j0);
+    SL_TRY(slab_pass<sl::dev::ROW_R2C>(P, j0, nf, coeffs, nullptr, nullptr, st));
+    SL_TRY(inv_acc_pass(P, g, j0, nf, st));
+  }
+  return inv_final(P, parts_used(P), use_invpsi, x, st);
+}
+
+// ------------------------------------------------- cluster-fused orchestration ---
+
+// x -> spectrum (one cluster) -> per filter C2R (all clusters).
+static sl_status cl_forward(const sl_bank* b, const float* x, float* coeffs, cudaStream_t st) {
+  ClArgs a{};
+  a.in_real = x;
+  a.out_spec = b->xhat_cl;
+  a.R = 1;
+  g_next_bytes = 4.0 * b->N;  // the signal is read once
+  SL_TRY(launched(b->cl->inv(1, st, a), "cluster_r2c"));
+  ClArgs f{};
+  f.xhat = b->xhat_cl;
+  f.psi = b->psi_cl;
+  f.out_real = coeffs;
+  f.R = b->R;
+  f.scale = (float)(1.0 / (double)b->N);
+  g_next_bytes = 4.0 * (double)b->R * (b->N + b->Nh);  // filters read, coefficients written
+  return launched(b->cl->fwd(b->ncl, st, f), "cluster_fwd_filters");
+}
+
+// coefficients -> per-cluster partial sums -> (sum, * 1/Psi) -> C2R (one cluster).
+static sl_status cl_backward(const sl_bank* b, const float* coeffs, float* x, bool use_invpsi,
+                             cudaStream_t st) {
+  ClArgs a{};
+  a.in_real = coeffs;
+  a.psi = b->psi_cl;
+  a.out_spec = b->part_cl;
+  a.R = b->R;
+  g_next_bytes = 4.0 * (double)b->R * (b->N + b->Nh);  // coefficients and filters read
+  SL_TRY(launched(b->cl->inv(b->ncl, st, a), "cluster_inv_filters"));
+  const int64_t T = b->cl->TOTAL;
+  const int grid = (int)std::min<int64_t>((T + 255) / 256, 4 * 148);
+  const float2* parts = b->part_cl;
+  const int np = b->ncl;
+  const double* w = use_invpsi ? b->invPsi_cl : nullptr;
+  float2* out = b->xhat_cl;
+  g_next_bytes = use_invpsi ? 8.0 * (double)b->Nh : 0.0;  // 1/Psi read
+  SL_TRY(launched(timed_launch("reduce_partials", st, [&]() {
+                    sl::dev::k_cl_reduce<<<grid, 256, 0, st>>>(parts, np, T, w, out);
+                  }),
+                  "reduce_partials"));
+  ClArgs f{};
+  f.xhat = b->xhat_cl;
+  f.out_real = x;
+  f.R = 1;
+  f.scale = (float)(1.0 / (double)b->N);
+  g_next_bytes = 4.0 * b->N;  // the signal is written once
+  return launched(b->cl->fwd(1, st, f), "cluster_c2r");
 }
 
 extern "C" {
@@ -663,27 +1073,22 @@ extern "C" {
 sl_status sl_forward(const sl_bank* b, const float* x, float* coeffs, void* stream) {
   SL_TRY(check_call(b));
   if (!x || !coeffs) return fail(SL_EINVAL, "x or coeffs is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  SL_TRY(spectrum_of(b, x, st));
-  for (int g = 0; g < b->ngroups; ++g) {
-    const int j0 = g * b->G;
-    const int nf = std::min(b->G, b->R - j0);
-    SL_TRY(fwd_filter_pass(b, j0, nf, st));
-    SL_TRY(slab_pass<sl::dev::ROW_C2R>(b, j0, nf, nullptr, coeffs, nullptr, st));
-  }
-  return SL_OK;
+  if (b->cl) return cl_forward(b, x, coeffs, (cudaStream_t)stream);
+  return forward_plan(plan_of(b), x, coeffs, (cudaStream_t)stream);
 }
 
 sl_status sl_adjoint(const sl_bank* b, const float* coeffs, float* x, void* stream) {
   SL_TRY(check_call(b));
   if (!x || !coeffs) return fail(SL_EINVAL, "x or coeffs is NULL");
-  return backward(b, coeffs, x, false, (cudaStream_t)stream);
+  if (b->cl) return cl_backward(b, coeffs, x, false, (cudaStream_t)stream);
+  return backward(plan_of(b), coeffs, x, false, (cudaStream_t)stream);
 }
 
 sl_status sl_inverse(const sl_bank* b, const float* coeffs, float* x, void* stream) {
   SL_TRY(check_call(b));
   if (!x || !coeffs) return fail(SL_EINVAL, "x or coeffs is NULL");
-  return backward(b, coeffs, x, true, (cudaStream_t)stream);
+  if (b->cl) return cl_backward(b, coeffs, x, true, (cudaStream_t)stream);
+  return backward(plan_of(b), coeffs, x, true, (cudaStream_t)stream);
 }
 
 sl_status sl_threshold(const sl_bank* b, float* coeffs, float sigma, const float* K,
@@ -699,13 +1104,13 @@ sl_status sl_threshold(const sl_bank* b, float* coeffs, float sigma, const float
     Thresholds t;
     fill_thresholds(b, j0, nf, sigma, K, &t);
     const int64_t n4 = b->N / 4;
-    int gx = (int)std::min<int64_t>((n4 + kThreads - 1) / kThreads, 64);
+    int gx = (int)std::min<int64_t>((n4 + 255) / 256, 64);
     dim3 g(std::max(gx, 1), nf);
     float* base = coeffs + (int64_t)j0 * b->N;
     const int64_t n = b->N;
     g_next_bytes = 8.0 * (double)n * nf;  // read and write
     SL_TRY(launched(timed_launch("threshold", st, [&]() {
-                      sl::dev::k_threshold<<<g, kThreads, 0, st>>>(base, n, nf, t);
+                      sl::dev::k_threshold<<<g, 256, 0, st>>>(base, n, nf, t);
                     }),
                     "threshold"));
   }
@@ -718,17 +1123,18 @@ sl_status sl_denoise(const sl_bank* b, const float* noisy, float* out, float sig
   if (!noisy || !out || !K) return fail(SL_EINVAL, "noisy, out or K is NULL");
   if (!(sigma >= 0.f) || !std::isfinite(sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
-  SL_TRY(spectrum_of(b, noisy, st));
-  for (int g = 0; g < b->ngroups; ++g) {
-    const int j0 = g * b->G;
-    const int nf = std::min(b->G, b->R - j0);
+  const Plan P = plan_of(b);
+  SL_TRY(spectrum_of(P, noisy, st));
+  for (int g = 0; g < P.ngroups; ++g) {
+    const int j0 = g * P.G;
+    const int nf = std::min(P.G, P.R - j0);
     Thresholds t;
     fill_thresholds(b, j0, nf, sigma, K, &t);
-    SL_TRY(fwd_filter_pass(b, j0, nf, st));
-    SL_TRY(slab_pass<sl::dev::ROW_RT>(b, j0, nf, nullptr, nullptr, &t, st));
-    SL_TRY(inv_acc_pass(b, g, j0, nf, st));
+    SL_TRY(fwd_filter_pass(P, j0, nf, st));
+    SL_TRY(slab_pass<sl::dev::ROW_RT>(P, j0, nf, nullptr, nullptr, &t, st));
+    SL_TRY(inv_acc_pass(P, g, j0, nf, st));
   }
-  return inv_final(b, parts_used(b), true, out, st);
+  return inv_final(P, parts_used(P), true, out, st);
 }
 
 sl_status sl_fwdinv_host(const sl_bank* cb, const float* x_host, float* y_host, void* stream) {
@@ -833,75 +1239,34 @@ extern "C" sl_status sl_forward_noalloc(const sl_bank* b, const float* psi, cons
   if (!b) return fail(SL_EINVAL, "bank is NULL");
   if (!psi || !x || !coeffs) return fail(SL_EINVAL, "psi, x or coeffs is NULL");
   const int64_t cap = (int64_t)(SL_NOALLOC_SCRATCH_BYTES / sizeof(float2));
-  if (2 * b->Nh > cap)
+  if (2 * b->Nhp > cap)
     return fail(SL_ENOTSUP, "sl_forward_noalloc: the signal's spectrum plus one filter's "
-                            "spectrum need " + std::to_string(2 * b->Nh * 8) +
+                            "spectrum need " + std::to_string(2 * b->Nhp * 8) +
                             " bytes, more than SL_NOALLOC_SCRATCH_BYTES (16 MiB)");
   int dev = -1;
   SL_CUDA(cudaGetDevice(&dev));
   SL_TRY(init_device(dev));
-  float2* xhat = nullptr;
-  SL_TRY(noalloc_scratch_ptr(dev, &xhat));
-  float2* slots = xhat + b->Nh;
-  const int G = (int)std::min<int64_t>({(cap - b->Nh) / b->Nh, (int64_t)kMaxGroup, (int64_t)b->R});
-  cudaStream_t st = (cudaStream_t)stream;
-  const sl::BankSpec& s = b->spec;
-  const int L0 = (int)s.dims[0];
-  const int NP = (int)(b->Nh / L0);
-  const int ctiles = (NP + col_tile(L0) - 1) / col_tile(L0);
-
-  // spectrum of x: last axes (rows or planes), then pencils along axis 0, in place
-  RowArgs ra{};
-  ra.in_real = x;
-  ra.out_half = xhat;
-  ra.scale = 1.f;
-  ra.nh = (int)s.nh();
-  ra.n_rows = L0;
-  if (s.ndim == 2) {
-    const int L1 = (int)s.dims[1];
-    dim3 g((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), 1);
-    SL_TRY(launched(launch_row<sl::dev::ROW_R2C>(L1, g, st, ra), "row_r2c"));
-  } else {
-    SL_TRY(launched(launch_plane<sl::dev::ROW_R2C>((int)s.dims[1], (int)s.dims[2], dim3(L0, 1),
-                                                   st, ra), "plane_r2c"));
-  }
-  ColArgs ca{};
-  ca.in = xhat;
-  ca.out = xhat;
-  ca.Nh = b->Nh;
-  ca.NP = NP;
-  SL_TRY(launched(launch_col<sl::dev::COL_SPEC>(L0, dim3(ctiles, 1), st, ca), "col_spec"));
-
-  // per group of G filters: pencils (x psi, inverse FFT) into the slots, then the
-  // last axes into the caller's coefficient planes
-  for (int j0 = 0; j0 < b->R; j0 += G) {
-    const int nf = std::min(G, b->R - j0);
-    ColArgs cf{};
-    cf.in = xhat;
-    cf.out = slots;
-    cf.psi = psi;
-    cf.Nh = b->Nh;
-    cf.NP = NP;
-    cf.j0 = j0;
-    cf.nfilt = nf;
-    SL_TRY(launched(launch_col<sl::dev::COL_FWD_FILT>(L0, dim3(ctiles, nf), st, cf),
-                    "col_fwd_filter"));
-    RowArgs rc{};
-    rc.in_half = slots;
-    rc.in_stride = b->Nh;
-    rc.out_real = coeffs + (int64_t)j0 * b->N;
-    rc.out_stride = b->N;
-    rc.scale = (float)(1.0 / (double)b->N);
-    rc.nh = (int)s.nh();
-    rc.n_rows = L0;
-    if (s.ndim == 2) {
-      const int L1 = (int)s.dims[1];
-      dim3 g((L0 / 2 + row_pairs_per_cta(L1) - 1) / row_pairs_per_cta(L1), nf);
-      SL_TRY(launched(launch_row<sl::dev::ROW_C2R>(L1, g, st, rc), "row_c2r"));
-    } else {
-      SL_TRY(launched(launch_plane<sl::dev::ROW_C2R>((int)s.dims[1], (int)s.dims[2],
-                                                     dim3(L0, nf), st, rc), "plane_c2r"));
-    }
-  }
-  return SL_OK;
+  float2* base = nullptr;
+  SL_TRY(noalloc_scratch_ptr(dev, &base));
+  // scratch layout: the spectrum of x, then G filter slots. Pad pencils may hold stale
+  // values from earlier calls; they never reach a result, because pencils are
+  // transformed independently and the last-axes passes read valid pencils only.
+  Plan P{};
+  P.spec = &b->spec;
+  P.N = b->N;
+  P.Nh = b->Nh;
+  P.Nhp = b->Nhp;
+  P.NP = b->NP;
+  P.TC = b->TC;
+  P.lgTC = b->lgTC;
+  P.ntiles = b->ntiles;
+  P.R = b->R;
+  P.G = (int)std::min<int64_t>({(cap - b->Nhp) / b->Nhp, (int64_t)kMaxGroup, (int64_t)b->R});
+  P.ngroups = (P.R + P.G - 1) / P.G;
+  P.psi = psi;
+  P.psi_natural = 1;
+  P.xhat = base;
+  P.scratch = base + b->Nhp;
+  P.bank = b;
+  return forward_plan(P, x, coeffs, (cudaStream_t)stream);
 }

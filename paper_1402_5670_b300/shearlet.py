@@ -33,11 +33,15 @@ SIGNATURES = {
     "sl_last_error": (ctypes.c_char_p, []),
     "sl_build_filters": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "sl_build_filters_ex": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.POINTER(_vp)]),
     "sl_free_filters": (None, [_vp]),
     "sl_bank_info": (ctypes.c_int, [_vp, _c_int_p, _c_int64_p, _c_int_p, _c_int_p]),
     "sl_bank_filter_meta": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
     "sl_bank_norms": (ctypes.c_int, [_vp, _c_double_p, _c_double_p, _c_double_p]),
     "sl_bank_sizes": (ctypes.c_int, [_vp, _c_int64_p, _c_int64_p]),
+    "sl_bank_path": (ctypes.c_int, [_vp, _c_int_p]),
     "sl_bank_eval_f64": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p]),
     "sl_bank_filters_f32": (ctypes.c_int, [_vp, _c_float_p]),
     "sl_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -102,6 +106,13 @@ def _dev_ptr(t, name: str, numel: int) -> int:
 
 # ------------------------------------------------------- C ABI, same names ---
 
+PATHS = {"auto": 0, "general": 1, "cluster": 2}
+
+
+class sl_options(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
 def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
                      full_system: bool = False, device: int = 0) -> int:
     nd = len(dims)
@@ -110,6 +121,19 @@ def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[
     out = _vp()
     _check(lib().sl_build_filters(nd, d, int(n_scales), sl, int(bool(full_system)), int(device),
                                   ctypes.byref(out)), "sl_build_filters")
+    return out.value
+
+
+def sl_build_filters_ex(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
+                        full_system: bool = False, device: int = 0, path: str = "auto") -> int:
+    nd = len(dims)
+    d = (ctypes.c_int64 * nd)(*[int(v) for v in dims])
+    sl = (ctypes.c_int * len(shear_levels))(*[int(v) for v in shear_levels])
+    opt = sl_options()
+    opt.path = PATHS[path]
+    out = _vp()
+    _check(lib().sl_build_filters_ex(nd, d, int(n_scales), sl, int(bool(full_system)), int(device),
+                                     ctypes.byref(opt), ctypes.byref(out)), "sl_build_filters_ex")
     return out.value
 
 
@@ -180,11 +204,12 @@ class Bank:
     """
 
     def __init__(self, dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
-                 full_system: bool = False, device: int = 0):
+                 full_system: bool = False, device: int = 0, path: str = "auto"):
         if device >= 0:
             import torch
             torch.cuda.set_device(device)
-        self.handle = sl_build_filters(dims, n_scales, shear_levels, full_system, device)
+        self.path = path
+        self.handle = sl_build_filters_ex(dims, n_scales, shear_levels, full_system, device, path)
         L = lib()
         nd, R, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         dd = (ctypes.c_int64 * 3)()
@@ -203,6 +228,9 @@ class Bank:
         _check(L.sl_bank_norms(self.handle, self.norms.ctypes.data_as(_c_double_p),
                                ctypes.byref(A), ctypes.byref(B)), "sl_bank_norms")
         self.A, self.B = A.value, B.value
+        pth = ctypes.c_int()
+        _check(L.sl_bank_path(self.handle, ctypes.byref(pth)), "sl_bank_path")
+        self.kernel_path = {1: "general", 2: "cluster"}[pth.value]
         self.scale_of = np.zeros(self.R, dtype=np.int32)
         self.cone_of = np.zeros(self.R, dtype=np.int32)
         self.k_of = np.zeros((self.R, 2), dtype=np.int32)

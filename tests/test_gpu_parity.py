@@ -35,11 +35,12 @@ def _cuda():
 _BANKS = {}
 
 
-def bank(dims, J, sl, full=False):
+def bank(dims, J, sl, full=False, path="general"):
     from paper_1402_5670_b300.shearlet import Bank
-    key = (tuple(dims), J, tuple(sl), full)
+    key = (tuple(dims), J, tuple(sl), full, path)
     if key not in _BANKS:
-        _BANKS[key] = Bank(dims, J, sl, full, device=0)
+        _BANKS[key] = Bank(dims, J, sl, full, device=0, path=path)
+        assert _BANKS[key].kernel_path == path
     return _BANKS[key]
 
 
@@ -128,9 +129,10 @@ def test_denoise_fused_matches_oracle(case):
     assert O.psnr(clean, den) > O.psnr(clean, noisy)
 
 
-def test_fwdinv_host_round_trip():
+@pytest.mark.parametrize("path", ["general", "cluster"])
+def test_fwdinv_host_round_trip(path):
     dims = (256, 256)
-    b = bank(dims, 2, (1, 1))
+    b = bank(dims, 2, (1, 1), path=path)
     x = signal(dims, 7)
     xh = torch.from_numpy(x).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -173,14 +175,48 @@ def test_repeated_calls_are_deterministic():
     assert torch.equal(b.inverse(C1), b.inverse(C2))
 
 
+# ----------------------------------------------- cluster-fused 2D path ---
+
+CLUSTER_CASES = [((64, 64), 2, (1, 1)), ((128, 256), 3, (1, 1, 2)), ((256, 128), 3, (0, 1, 1)),
+                 ((512, 64), 2, (1, 1)), ((64, 512), 2, (1, 2)), ((256, 512), 4, (1, 1, 2, 2))]
+
+
+@pytest.mark.parametrize("case", CLUSTER_CASES, ids=str)
+def test_cluster_path_matches_oracle(case):
+    """The cluster-fused kernels (8 CTAs share one spectrum through distributed shared
+    memory) against the oracle: forward, inverse and adjoint."""
+    dims, J, sl = case
+    b = bank(dims, J, sl, path="cluster")
+    s = oracle_system(dims, J, sl)
+    x = signal(dims, 12)
+    C = b.forward(cuda(x)).cpu().numpy()
+    assert rel(C, O.forward(x.astype(np.float64), s)) < TOL
+    Cf = C.astype(np.float64)
+    assert rel(b.inverse(cuda(C)).cpu().numpy(), O.inverse(Cf, s)) < TOL
+    Cr = synth.gaussian_field((b.R,) + tuple(dims), 13)
+    assert rel(b.adjoint(cuda(Cr)).cpu().numpy(), O.adjoint(Cr.astype(np.float64), s)) < TOL
+
+
+def test_cluster_path_is_deterministic_and_agrees_with_general():
+    dims, J, sl = (256, 256), 2, (1, 1)
+    bc = bank(dims, J, sl, path="cluster")
+    bg = bank(dims, J, sl, path="general")
+    xg = cuda(signal(dims, 14))
+    C1, C2 = bc.forward(xg).clone(), bc.forward(xg)
+    assert torch.equal(C1, C2)
+    assert torch.equal(bc.inverse(C1), bc.inverse(C2))
+    assert rel(C1.cpu().numpy(), bg.forward(xg).cpu().numpy()) < TOL
+
+
 # ------------------------------------------------ full-size configurations ---
 
 
-def test_full_size_2d_512():
+@pytest.mark.parametrize("path", ["general", "cluster"])
+def test_full_size_2d_512(path):
     """512^2, four scales, levels (1,1,2,2): R = 49 — the benchmark configuration,
-    compared element by element (forward, inverse, denoise)."""
+    compared element by element (forward, inverse), on both kernel paths."""
     dims, J, sl = (512, 512), 4, (1, 1, 2, 2)
-    b = bank(dims, J, sl)
+    b = bank(dims, J, sl, path=path)
     s = oracle_system(dims, J, sl)
     assert b.R == 49
     x = signal(dims, 10)
