@@ -208,6 +208,50 @@ sl_status sl_forward_noalloc(const sl_bank* bank, const float* psi, const float*
                              float* coeffs, void* stream);
 
 /*
+ * Learned shrinkage (no counterpart in the paper's method; it replaces the hard
+ * threshold of Sec. 5.3, which stays available as sl_threshold / sl_denoise). A small
+ * MLP predicts a gain g in [0, 1] per coefficient of subband j >= 1 from
+ *   x = [c/s, |c(m+d)|/s for d in {-1,0,1}^ndim (row-major, periodic), E_j]
+ * with s = sigma ||psi_j||_2 and E_j a learned 8-vector per subband:
+ *   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), g = sigmoid(w3 . h2 + b3),
+ * and the coefficient becomes g c. Width 64; products on the tensor cores in BF16
+ * with FP32 accumulation; FP32 master parameters trained with Adam on the GPU.
+ * Flat FP32 parameter layout (host arrays of sl_mlp_num_params floats), F = 1 + 3^ndim + 8:
+ *   W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3[1], E[R][8].
+ * Training loss on a sample of coefficients: mean(((g c - c_clean) / s)^2).
+ */
+typedef struct sl_mlp sl_mlp;
+
+/* Create an MLP for a device bank (parameters start at zero; set them with
+ * sl_mlp_set_params). The bank must outlive the MLP. */
+sl_status sl_mlp_create(const sl_bank* bank, sl_mlp** out);
+void sl_mlp_free(sl_mlp* mlp);
+int sl_mlp_num_params(const sl_mlp* mlp);
+/* Host <-> device copies of the flat parameters; set also resets Adam's state. */
+sl_status sl_mlp_set_params(sl_mlp* mlp, const float* host);
+sl_status sl_mlp_get_params(const sl_mlp* mlp, float* host);
+/* Gradients of the loss over the n samples idx (DEVICE int32 flat indices
+ * q = j * N + m with j >= 1; n a positive multiple of 128) of the DEVICE coefficient
+ * stacks noisy and clean [R][dims], copied to grad_host[num_params] and *loss_host
+ * (either may be NULL). Synchronises the stream. */
+sl_status sl_mlp_gradients(sl_mlp* mlp, const float* noisy, const float* clean, float sigma,
+                           const int* idx, int n, float* grad_host, float* loss_host,
+                           void* stream);
+/* One training step: gradients as above, then an Adam update (beta1 0.9, beta2 0.999,
+ * eps 1e-8, learning rate lr). The sample's loss (before the update) is written to
+ * the DEVICE float loss_dev if not NULL. Asynchronous. */
+sl_status sl_mlp_train_step(sl_mlp* mlp, const float* noisy, const float* clean, float sigma,
+                            const int* idx, int n, float lr, float* loss_dev, void* stream);
+/* out[j] = g * coeffs[j] for every subband j >= 1 and out[0] = coeffs[0] (DEVICE
+ * [R][dims]; out must not alias coeffs, whose neighbourhoods the features read). */
+sl_status sl_mlp_apply(sl_mlp* mlp, const float* coeffs, float* out, float sigma, void* stream);
+/* Learned denoising: sl_forward, sl_mlp_apply, sl_inverse (DEVICE [dims] arrays; the
+ * first call allocates 2 R N floats of coefficient memory kept by the MLP). */
+sl_status sl_mlp_denoise(sl_mlp* mlp, const float* noisy, float* out, float sigma, void* stream);
+/* Text of the last MLP error on the calling thread. */
+const char* sl_mlp_last_error(void);
+
+/*
  * Kernel timing for profiling. When enabled, every kernel launch of the library is
  * bracketed by CUDA events recorded on the launch stream; sl_profile_read returns,
  * per kernel kind, the number of launches, their summed device time (ms) and their

@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libshearlet.so")
-SOURCES = ["shearlet.cu", "bank_host.cpp"]
-HEADERS = ["fft_core.cuh", "kernels2d.cuh", "kernels3d.cuh", "bank_host.h"]
+SOURCES = ["shearlet.cu", "bank_host.cpp", "mlp.cu"]
+HEADERS = ["fft_core.cuh", "kernels2d.cuh", "kernels3d.cuh", "kernels_cluster.cuh", "bank_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,798 @@
+// Learned shrinkage: a small MLP that predicts a gain g in [0, 1] per shearlet
+// coefficient from the coefficient, its neighbourhood magnitudes and a learned
+// subband embedding, replacing the hard threshold of the paper's denoiser
+// (eq. hard_tresholding, Sec. 5.3). Training (forward, backward, Adam) and inference
+// run in these kernels; the products run on the tensor cores as BF16 mma.sync with
+// FP32 accumulation, master weights stay FP32.
+//
+// Network (F = 1 + 3^ndim + 8 features, padded to KP = F rounded up to 16):
+//   x = [c/s, |c(m+d)|/s for d in {-1,0,1}^ndim (row-major, periodic), E_j]
+//   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), g = sigmoid(w3 . h2 + b3), c_hat = g c
+// with s = sigma ||psi_j||_2. Loss on a sample: mean(((g c - c_clean) / s)^2).
+//
+// Tiles: a warp handles 16 coefficients (the M = 16 rows of m16n8k16); the hidden
+// width 64 is 8 n-tiles of 8. Fragment layouts (lane = 4 * gid + tig):
+//   A 16x16: a0 = (gid, 2tig..+1), a1 = (gid+8, 2tig..+1), a2 = (gid, 2tig+8..+9),
+//            a3 = (gid+8, 2tig+8..+9);   B 16x8: b0 = (k 2tig..+1, n gid), b1 = (k 2tig+8..+9, n gid)
+//   C 16x8 : c0,c1 = (gid, 2tig..+1), c2,c3 = (gid+8, 2tig..+1).
+// Two adjacent C n-tiles of one layer are exactly the A fragment of one k-slice of
+// the next product, so activations stay in registers.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/shearlet.h"
+
+namespace {
+
+constexpr int H = 64;   // hidden width
+constexpr int EMB = 8;  // subband embedding
+constexpr int WARPS = 8;
+constexpr int ROWS = 16 * WARPS;  // coefficients per CTA tile
+
+template <int NDIM>
+struct Net {
+  static constexpr int NB = NDIM == 2 ? 9 : 27;
+  static constexpr int F = 1 + NB + EMB;
+  static constexpr int KP = (F + 15) / 16 * 16;
+  static constexpr int KS = KP / 16;
+  // flat parameter offsets
+  static constexpr int oW1 = 0, ob1 = oW1 + H * F, oW2 = ob1 + H, ob2 = oW2 + H * H,
+                       ow3 = ob2 + H, ob3 = ow3 + H, oE = ob3 + 1;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Shared-memory weights of one CTA: BF16 copies, row-major with padded rows.
+template <int NDIM>
+struct SmemW {
+  static constexpr int KP = Net<NDIM>::KP;
+  static constexpr int P1 = KP + 8;  // row pitch (bf16) of W1 [H][KP]
+  static constexpr int P2 = H + 8;   // row pitch of W2 [H][H] and its transpose
+  __nv_bfloat16 W1[H * P1];          // W1[o][k]
+  __nv_bfloat16 W1T[KP * (H + 8)];   // W1T[k][o]
+  __nv_bfloat16 W2[H * P2];          // W2[o][i]
+  __nv_bfloat16 W2T[H * P2];         // W2T[i][o]
+  float b1[H], b2[H], w3[H];
+  float b3;
+};
+
+template <int NDIM>
+__device__ void load_weights(SmemW<NDIM>& s, const float* __restrict__ prm) {
+  using N = Net<NDIM>;
+  constexpr int F = N::F, KP = N::KP;
+  for (int i = threadIdx.x; i < H * KP; i += blockDim.x) {
+    const int o = i / KP, k = i % KP;
+    const float w = k < F ? prm[N::oW1 + o * F + k] : 0.f;
+    s.W1[o * SmemW<NDIM>::P1 + k] = __float2bfloat16_rn(w);
+    s.W1T[k * (H + 8) + o] = __float2bfloat16_rn(w);
+  }
+  for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
+    const int o = i / H, k = i % H;
+    const float w = prm[N::oW2 + i];
+    s.W2[o * SmemW<NDIM>::P2 + k] = __float2bfloat16_rn(w);
+    s.W2T[k * SmemW<NDIM>::P2 + o] = __float2bfloat16_rn(w);
+  }
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    s.b1[i] = prm[N::ob1 + i];
+    s.b2[i] = prm[N::ob2 + i];
+    s.w3[i] = prm[N::ow3 + i];
+  }
+  if (threadIdx.x == 0) s.b3 = prm[N::ob3];
+}
+
+struct Geom {
+  int dims[3];  // grid
+  int lg[3];    // log2 of dims
+  int64_t N;    // points per subband
+};
+
+// Flat coefficient index q = j * N + m; the neighbour of m at offset index t
+// (row-major over {-1, 0, 1}^ndim) with periodic wrap.
+template <int NDIM>
+__device__ __forceinline__ int64_t neighbour(const Geom& g, int64_t q, int t) {
+  const int64_t m = q & (g.N - 1);
+  const int64_t base = q - m;
+  if constexpr (NDIM == 2) {
+    const int i0 = (int)(m >> g.lg[1]), i1 = (int)(m & (g.dims[1] - 1));
+    const int d0 = t / 3 - 1, d1 = t % 3 - 1;
+    const int n0 = (i0 + d0) & (g.dims[0] - 1), n1 = (i1 + d1) & (g.dims[1] - 1);
+    return base + ((int64_t)n0 << g.lg[1]) + n1;
+  } else {
+    const int i0 = (int)(m >> (g.lg[1] + g.lg[2]));
+    const int i1 = (int)((m >> g.lg[2]) & (g.dims[1] - 1));
+    const int i2 = (int)(m & (g.dims[2] - 1));
+    const int d0 = t / 9 - 1, d1 = (t / 3) % 3 - 1, d2 = t % 3 - 1;
+    const int n0 = (i0 + d0) & (g.dims[0] - 1), n1 = (i1 + d1) & (g.dims[1] - 1),
+              n2 = (i2 + d2) & (g.dims[2] - 1);
+    return base + ((((int64_t)n0 << g.lg[1]) + n1) << g.lg[2]) + n2;
+  }
+}
+
+// Feature k of coefficient q (subband j, scale s), in FP32.
+template <int NDIM>
+__device__ __forceinline__ float feature(const Geom& g, const float* __restrict__ C, int64_t q,
+                                         int j, float inv_s, const float* __restrict__ E, int k) {
+  using N = Net<NDIM>;
+  if (k == 0) return C[q] * inv_s;
+  if (k <= N::NB) return fabsf(C[neighbour<NDIM>(g, q, k - 1)]) * inv_s;
+  if (k <= N::NB + EMB) return E[j * EMB + (k - N::NB - 1)];
+  return 0.f;
+}
+
+// Forward of one warp tile (16 coefficients, rows gid and gid+8 of this thread).
+// Outputs: g for both rows; optionally the intermediates for backward.
+template <int NDIM, bool TRAIN>
+struct Fwd {
+  uint32_t A1[Net<NDIM>::KS][4];  // features (bf16 A fragments)
+  uint32_t A2[4][4];              // h1 (bf16 A fragments, 4 k-slices of 16)
+  float z1[8][4], z2[8][4];       // pre-activations (C layout)
+  float z3[2], g[2];
+};
+
+template <int NDIM, bool TRAIN>
+__device__ __forceinline__ void mlp_forward(const SmemW<NDIM>& s, Fwd<NDIM, TRAIN>& f,
+                                            const Geom& geo, const float* __restrict__ C,
+                                            const int64_t (&q)[2], const int (&j)[2],
+                                            const float (&inv_s)[2],
+                                            const float* __restrict__ E) {
+  using N = Net<NDIM>;
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  // features -> A fragments
+#pragma unroll
+  for (int ks = 0; ks < N::KS; ++ks) {
+    float v[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          v[r][2 * h + e] = feature<NDIM>(geo, C, q[r], j[r], inv_s[r], E, 16 * ks + 8 * h + 2 * tig + e);
+    f.A1[ks][0] = pack_bf16(v[0][0], v[0][1]);
+    f.A1[ks][1] = pack_bf16(v[1][0], v[1][1]);
+    f.A1[ks][2] = pack_bf16(v[0][2], v[0][3]);
+    f.A1[ks][3] = pack_bf16(v[1][2], v[1][3]);
+  }
+  // layer 1
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int n0 = 8 * nt + 2 * tig;
+    float d[4] = {s.b1[n0], s.b1[n0 + 1], s.b1[n0], s.b1[n0 + 1]};
+#pragma unroll
+    for (int ks = 0; ks < N::KS; ++ks) {
+      const __nv_bfloat16* w = s.W1 + (8 * nt + gid) * SmemW<NDIM>::P1 + 16 * ks + 2 * tig;
+      mma16816(d, f.A1[ks], *reinterpret_cast<const uint32_t*>(w),
+               *reinterpret_cast<const uint32_t*>(w + 8));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f.z1[nt][i] = d[i];
+  }
+  // h1 = relu(z1) -> A fragments of layer 2
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const float(&lo)[4] = f.z1[2 * ks];
+    const float(&hi)[4] = f.z1[2 * ks + 1];
+    f.A2[ks][0] = pack_bf16(fmaxf(lo[0], 0.f), fmaxf(lo[1], 0.f));
+    f.A2[ks][1] = pack_bf16(fmaxf(lo[2], 0.f), fmaxf(lo[3], 0.f));
+    f.A2[ks][2] = pack_bf16(fmaxf(hi[0], 0.f), fmaxf(hi[1], 0.f));
+    f.A2[ks][3] = pack_bf16(fmaxf(hi[2], 0.f), fmaxf(hi[3], 0.f));
+  }
+  // layer 2 and the dot with w3
+  float part[2] = {0.f, 0.f};
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int n0 = 8 * nt + 2 * tig;
+    float d[4] = {s.b2[n0], s.b2[n0 + 1], s.b2[n0], s.b2[n0 + 1]};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const __nv_bfloat16* w = s.W2 + (8 * nt + gid) * SmemW<NDIM>::P2 + 16 * ks + 2 * tig;
+      mma16816(d, f.A2[ks], *reinterpret_cast<const uint32_t*>(w),
+               *reinterpret_cast<const uint32_t*>(w + 8));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f.z2[nt][i] = d[i];
+    part[0] += fmaxf(d[0], 0.f) * s.w3[n0] + fmaxf(d[1], 0.f) * s.w3[n0 + 1];
+    part[1] += fmaxf(d[2], 0.f) * s.w3[n0] + fmaxf(d[3], 0.f) * s.w3[n0 + 1];
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    float z = part[r];
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    f.z3[r] = z + s.b3;
+    f.g[r] = 1.f / (1.f + expf(-f.z3[r]));
+  }
+}
+
+struct MlpArgs {
+  const float* prm;   // master parameters (FP32, flat)
+  const float* C;     // noisy coefficients [R][N]
+  const float* Cc;    // clean coefficients (training)
+  float* out;         // inference output [R][N] (never aliases C)
+  const int* idx;     // training sample: flat indices q = j N + m, j >= 1
+  int n;              // samples (multiple of 128) or tiles
+  const float* inv_s; // [R] 1 / (sigma ||psi_j||)
+  float* grad;        // gradient accumulators (FP32, flat, zeroed by the caller)
+  float* loss;        // loss accumulator (device scalar)
+  Geom geo;
+  int R;
+};
+
+// Inference over all subbands j >= 1: out[j][m] = g * C[j][m]; out[0] = C[0].
+template <int NDIM>
+__global__ void __launch_bounds__(32 * WARPS) k_mlp_apply(MlpArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SmemW<NDIM>& s = *reinterpret_cast<SmemW<NDIM>*>(smraw);
+  load_weights<NDIM>(s, a.prm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int warp = threadIdx.x >> 5;
+  const float* E = a.prm + Net<NDIM>::oE;
+  const int64_t tiles = (int64_t)(a.R - 1) * (a.geo.N / 16);
+  for (int64_t t = (int64_t)blockIdx.x * WARPS + warp; t < tiles; t += (int64_t)gridDim.x * WARPS) {
+    const int64_t q0 = a.geo.N + t * 16;  // subbands 1.. are contiguous after subband 0
+    const int jj = (int)(q0 / a.geo.N);
+    int64_t q[2] = {q0 + gid, q0 + gid + 8};
+    int j[2] = {jj, jj};
+    float is[2] = {a.inv_s[jj], a.inv_s[jj]};
+    Fwd<NDIM, false> f;
+    mlp_forward<NDIM, false>(s, f, a.geo, a.C, q, j, is, E);
+    if (tig == 0) {
+      a.out[q[0]] = f.g[0] * a.C[q[0]];
+      a.out[q[1]] = f.g[1] * a.C[q[1]];
+    }
+  }
+  // the lowpass passes through
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.geo.N;
+         i += (int64_t)gridDim.x * blockDim.x)
+      a.out[i] = a.C[i];
+}
+
+// Training: forward and backward on a sample; gradients accumulate into a.grad.
+// Each CTA takes tiles of ROWS = 128 samples (16 per warp). The weight gradients
+// dW2 = sum dz2^T h1 and dW1 = sum dz1^T x are products over the sample dimension:
+// every warp stages its tile transposed in shared memory, and after a barrier the 8
+// warps multiply the CTA's 128 rows on the tensor cores, each warp owning a slice of
+// the output tiles and accumulating it over all tiles of the CTA in registers.
+template <int NDIM>
+struct TrainSmem {
+  static constexpr int KP = Net<NDIM>::KP;
+  static constexpr int PB = ROWS + 8;   // pitch (bf16) of the staged [.][ROWS] tiles
+  SmemW<NDIM> w;
+  __nv_bfloat16 dz2T[H * PB];           // dz2T[o][b]
+  __nv_bfloat16 h1T[H * PB];            // h1T[i][b]
+  __nv_bfloat16 dz1T[H * PB];           // dz1T[o][b]
+  __nv_bfloat16 xT[KP * PB];            // xT[k][b]
+};
+
+template <int NDIM>
+__global__ void __launch_bounds__(32 * WARPS) k_mlp_train(MlpArgs a) {
+  using N = Net<NDIM>;
+  using TS = TrainSmem<NDIM>;
+  constexpr int KP = N::KP, KS = N::KS, PB = TS::PB;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TS& S = *reinterpret_cast<TS*>(smraw);
+  load_weights<NDIM>(S.w, a.prm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int warp = threadIdx.x >> 5;
+  const float* E = a.prm + N::oE;
+  // per-warp slices of the weight-gradient tiles: dW2 has 4 x 8 tiles of 16 x 8
+  // (4 per warp), dW1 has 4 x (KP/8) tiles (KP/16 per warp... distributed round-robin)
+  constexpr int T2 = 4 * 8 / WARPS;        // 4
+  constexpr int NT1 = KP / 8;              // n-tiles of dW1
+  constexpr int T1 = (4 * NT1 + WARPS - 1) / WARPS;
+  float acc2[T2][4], acc1[T1][4];
+#pragma unroll
+  for (int i = 0; i < T2; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc2[i][e] = 0.f;
+#pragma unroll
+  for (int i = 0; i < T1; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc1[i][e] = 0.f;
+  float gw3[8][2], gb2[8][2], gb1[8][2], gb3 = 0.f, lsum = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) gw3[nt][e] = gb2[nt][e] = gb1[nt][e] = 0.f;
+  const float inv_n = 1.f / (float)a.n;
+  const int ntiles = a.n / ROWS;
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int r0 = tile * ROWS + warp * 16;
+    // sample indices are clamped to subbands 1..R-1 so that a bad index cannot read
+    // outside the stacks (the API requires valid indices)
+    const int64_t qlo = a.geo.N, qhi = (int64_t)a.R * a.geo.N - 1;
+    int64_t q[2] = {min(max((int64_t)a.idx[r0 + gid], qlo), qhi),
+                    min(max((int64_t)a.idx[r0 + gid + 8], qlo), qhi)};
+    int j[2] = {(int)(q[0] / a.geo.N), (int)(q[1] / a.geo.N)};
+    float is[2] = {a.inv_s[j[0]], a.inv_s[j[1]]};
+    Fwd<NDIM, true> f;
+    mlp_forward<NDIM, true>(S.w, f, a.geo, a.C, q, j, is, E);
+    // loss and dz3 (per row; the four threads of a row group hold the same values)
+    float dz3[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const float c = a.C[q[r]], cc = a.Cc[q[r]];
+      const float res = (f.g[r] * c - cc) * is[r];
+      if (tig == 0) lsum += res * res;
+      const float dg = 2.f * res * c * is[r] * inv_n;
+      dz3[r] = dg * f.g[r] * (1.f - f.g[r]);
+    }
+    if (tig == 0) gb3 += dz3[0] + dz3[1];
+    // dz2 = dz3 w3 [z2 > 0]; w3, b2 gradients; A fragments of dz2
+    uint32_t D2[4][4];
+    float dz2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int n0 = 8 * nt + 2 * tig;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = e >> 1, n = n0 + (e & 1);
+        const float z = f.z2[nt][e];
+        gw3[nt][e & 1] += fmaxf(z, 0.f) * dz3[r];
+        dz2[nt][e] = z > 0.f ? dz3[r] * S.w.w3[n] : 0.f;
+        gb2[nt][e & 1] += dz2[nt][e];
+      }
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      D2[ks][0] = pack_bf16(dz2[2 * ks][0], dz2[2 * ks][1]);
+      D2[ks][1] = pack_bf16(dz2[2 * ks][2], dz2[2 * ks][3]);
+      D2[ks][2] = pack_bf16(dz2[2 * ks + 1][0], dz2[2 * ks + 1][1]);
+      D2[ks][3] = pack_bf16(dz2[2 * ks + 1][2], dz2[2 * ks + 1][3]);
+    }
+    // dh1 = dz2 W2 (B[k = o][n = i] = W2[o][i] = W2T[i][o]); dz1 = dh1 [z1 > 0]
+    float dz1[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const __nv_bfloat16* w = S.w.W2T + (8 * nt + gid) * SmemW<NDIM>::P2 + 16 * ks + 2 * tig;
+        mma16816(d, D2[ks], *reinterpret_cast<const uint32_t*>(w),
+                 *reinterpret_cast<const uint32_t*>(w + 8));
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        dz1[nt][e] = f.z1[nt][e] > 0.f ? d[e] : 0.f;
+        gb1[nt][e & 1] += dz1[nt][e];
+      }
+    }
+    // dx for the embedding features: dx = dz1 W1 (B[k = o][n = f] = W1T[f][o])
+    {
+      uint32_t D1[4][4];
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        D1[ks][0] = pack_bf16(dz1[2 * ks][0], dz1[2 * ks][1]);
+        D1[ks][1] = pack_bf16(dz1[2 * ks][2], dz1[2 * ks][3]);
+        D1[ks][2] = pack_bf16(dz1[2 * ks + 1][0], dz1[2 * ks + 1][1]);
+        D1[ks][3] = pack_bf16(dz1[2 * ks + 1][2], dz1[2 * ks + 1][3]);
+      }
+      constexpr int e0 = N::NB + 1;       // first embedding feature
+      constexpr int nt0 = e0 / 8, nt1 = (e0 + EMB - 1) / 8;
+#pragma unroll
+      for (int nt = nt0; nt <= nt1; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const __nv_bfloat16* w = S.w.W1T + (8 * nt + gid) * (H + 8) + 16 * ks + 2 * tig;
+          mma16816(d, D1[ks], *reinterpret_cast<const uint32_t*>(w),
+                   *reinterpret_cast<const uint32_t*>(w + 8));
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int fcol = 8 * nt + 2 * tig + (e & 1);
+          if (fcol >= e0 && fcol < e0 + EMB)
+            atomicAdd(a.grad + N::oE + j[e >> 1] * EMB + (fcol - e0), d[e]);
+        }
+      }
+    }
+    // stage transposed bf16 tiles for the weight-gradient products
+    const int b0 = warp * 16 + gid, b1 = b0 + 8;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int o = 8 * nt + 2 * tig;
+      S.dz2T[o * PB + b0] = __float2bfloat16_rn(dz2[nt][0]);
+      S.dz2T[(o + 1) * PB + b0] = __float2bfloat16_rn(dz2[nt][1]);
+      S.dz2T[o * PB + b1] = __float2bfloat16_rn(dz2[nt][2]);
+      S.dz2T[(o + 1) * PB + b1] = __float2bfloat16_rn(dz2[nt][3]);
+      S.dz1T[o * PB + b0] = __float2bfloat16_rn(dz1[nt][0]);
+      S.dz1T[(o + 1) * PB + b0] = __float2bfloat16_rn(dz1[nt][1]);
+      S.dz1T[o * PB + b1] = __float2bfloat16_rn(dz1[nt][2]);
+      S.dz1T[(o + 1) * PB + b1] = __float2bfloat16_rn(dz1[nt][3]);
+      S.h1T[o * PB + b0] = __float2bfloat16_rn(fmaxf(f.z1[nt][0], 0.f));
+      S.h1T[(o + 1) * PB + b0] = __float2bfloat16_rn(fmaxf(f.z1[nt][1], 0.f));
+      S.h1T[o * PB + b1] = __float2bfloat16_rn(fmaxf(f.z1[nt][2], 0.f));
+      S.h1T[(o + 1) * PB + b1] = __float2bfloat16_rn(fmaxf(f.z1[nt][3], 0.f));
+    }
+    // features (already bf16 in the A fragments): A1[ks][0] = (row gid, k 16ks+2tig..+1) ...
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const uint32_t* fr = f.A1[ks];
+      const __nv_bfloat16* h0 = reinterpret_cast<const __nv_bfloat16*>(&fr[0]);
+      const __nv_bfloat16* h1 = reinterpret_cast<const __nv_bfloat16*>(&fr[1]);
+      const __nv_bfloat16* h2 = reinterpret_cast<const __nv_bfloat16*>(&fr[2]);
+      const __nv_bfloat16* h3 = reinterpret_cast<const __nv_bfloat16*>(&fr[3]);
+      const int k0 = 16 * ks + 2 * tig;
+      S.xT[k0 * PB + b0] = h0[0];
+      S.xT[(k0 + 1) * PB + b0] = h0[1];
+      S.xT[k0 * PB + b1] = h1[0];
+      S.xT[(k0 + 1) * PB + b1] = h1[1];
+      S.xT[(k0 + 8) * PB + b0] = h2[0];
+      S.xT[(k0 + 9) * PB + b0] = h2[1];
+      S.xT[(k0 + 8) * PB + b1] = h3[0];
+      S.xT[(k0 + 9) * PB + b1] = h3[1];
+    }
+    __syncthreads();
+    // dW2[o][i] += sum_b dz2T[o][b] h1T[i][b]: A = dz2T (row o, col b), B[k=b][n=i] = h1T[i][b]
+#pragma unroll
+    for (int t = 0; t < T2; ++t) {
+      const int id = warp * T2 + t;  // 0..31
+      const int mt = id / 8, nt = id % 8;
+#pragma unroll
+      for (int ks = 0; ks < ROWS / 16; ++ks) {
+        const __nv_bfloat16* ar = S.dz2T + (16 * mt + gid) * PB + 16 * ks + 2 * tig;
+        uint32_t af[4] = {*reinterpret_cast<const uint32_t*>(ar),
+                          *reinterpret_cast<const uint32_t*>(ar + 8 * PB),
+                          *reinterpret_cast<const uint32_t*>(ar + 8),
+                          *reinterpret_cast<const uint32_t*>(ar + 8 * PB + 8)};
+        const __nv_bfloat16* br = S.h1T + (8 * nt + gid) * PB + 16 * ks + 2 * tig;
+        mma16816(acc2[t], af, *reinterpret_cast<const uint32_t*>(br),
+                 *reinterpret_cast<const uint32_t*>(br + 8));
+      }
+    }
+    // dW1[o][k] += sum_b dz1T[o][b] xT[k][b]
+#pragma unroll
+    for (int t = 0; t < T1; ++t) {
+      const int id = warp + WARPS * t;  // 0 .. 4*NT1-1
+      if (id < 4 * NT1) {
+        const int mt = id / NT1, nt = id % NT1;
+#pragma unroll
+        for (int ks = 0; ks < ROWS / 16; ++ks) {
+          const __nv_bfloat16* ar = S.dz1T + (16 * mt + gid) * PB + 16 * ks + 2 * tig;
+          uint32_t af[4] = {*reinterpret_cast<const uint32_t*>(ar),
+                            *reinterpret_cast<const uint32_t*>(ar + 8 * PB),
+                            *reinterpret_cast<const uint32_t*>(ar + 8),
+                            *reinterpret_cast<const uint32_t*>(ar + 8 * PB + 8)};
+          const __nv_bfloat16* br = S.xT + (8 * nt + gid) * PB + 16 * ks + 2 * tig;
+          mma16816(acc1[t], af, *reinterpret_cast<const uint32_t*>(br),
+                   *reinterpret_cast<const uint32_t*>(br + 8));
+        }
+      }
+    }
+    __syncthreads();  // staging reused by the next tile
+  }
+  // flush this CTA's gradients
+  float* gr = a.grad;
+#pragma unroll
+  for (int t = 0; t < T2; ++t) {
+    const int id = warp * T2 + t, mt = id / 8, nt = id % 8;
+    const int o = 16 * mt + gid, i = 8 * nt + 2 * tig;
+    atomicAdd(gr + N::oW2 + o * H + i, acc2[t][0]);
+    atomicAdd(gr + N::oW2 + o * H + i + 1, acc2[t][1]);
+    atomicAdd(gr + N::oW2 + (o + 8) * H + i, acc2[t][2]);
+    atomicAdd(gr + N::oW2 + (o + 8) * H + i + 1, acc2[t][3]);
+  }
+#pragma unroll
+  for (int t = 0; t < T1; ++t) {
+    const int id = warp + WARPS * t;
+    if (id < 4 * NT1) {
+      const int mt = id / NT1, nt = id % NT1;
+      const int o = 16 * mt + gid, k = 8 * nt + 2 * tig;
+      if (k < N::F) {
+        atomicAdd(gr + N::oW1 + o * N::F + k, acc1[t][0]);
+        atomicAdd(gr + N::oW1 + (o + 8) * N::F + k, acc1[t][2]);
+      }
+      if (k + 1 < N::F) {
+        atomicAdd(gr + N::oW1 + o * N::F + k + 1, acc1[t][1]);
+        atomicAdd(gr + N::oW1 + (o + 8) * N::F + k + 1, acc1[t][3]);
+      }
+    }
+  }
+  // bias and w3 gradients: reduce over the 8 row groups of the warp, then atomics
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float v1 = gw3[nt][e], v2 = gb2[nt][e], v3 = gb1[nt][e];
+#pragma unroll
+      for (int sft = 4; sft < 32; sft <<= 1) {
+        v1 += __shfl_xor_sync(0xffffffffu, v1, sft);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, sft);
+        v3 += __shfl_xor_sync(0xffffffffu, v3, sft);
+      }
+      if (gid == 0) {
+        const int n = 8 * nt + 2 * tig + e;
+        atomicAdd(gr + N::ow3 + n, v1);
+        atomicAdd(gr + N::ob2 + n, v2);
+        atomicAdd(gr + N::ob1 + n, v3);
+      }
+    }
+#pragma unroll
+  for (int sft = 4; sft < 32; sft <<= 1) {
+    gb3 += __shfl_xor_sync(0xffffffffu, gb3, sft);
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, sft);
+  }
+  if (lane == 0) {
+    atomicAdd(gr + N::ob3, gb3);
+    atomicAdd(a.loss, lsum * inv_n);
+  }
+}
+
+// Adam (Kingma & Ba) on the flat parameters; t counts from 1.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float c1, float c2) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+thread_local std::string g_mlp_err;
+
+sl_status mfail(sl_status s, const std::string& msg) {
+  g_mlp_err = msg;
+  return s;
+}
+
+}  // namespace
+
+struct sl_mlp {
+  const sl_bank* bank = nullptr;
+  int ndim = 2, R = 0;
+  Geom geo{};
+  int P = 0;  // parameters
+  float* prm = nullptr;
+  float* grad = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* loss = nullptr;
+  float* inv_s = nullptr;  // [R]
+  float* coeffs = nullptr; // [2][R][N] for sl_mlp_denoise (allocated on first use)
+  std::vector<double> norms;
+  int t = 0;
+  float sigma_set = -1.f;
+};
+
+static int lg2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+static int n_params(int ndim, int R) {
+  const int F = 1 + (ndim == 2 ? 9 : 27) + EMB;
+  return H * F + H + H * H + H + H + 1 + R * EMB;
+}
+
+template <int NDIM>
+static size_t train_smem() { return sizeof(TrainSmem<NDIM>); }
+template <int NDIM>
+static size_t apply_smem() { return sizeof(SmemW<NDIM>); }
+
+static sl_status set_sigma(sl_mlp* M, float sigma, cudaStream_t st) {
+  if (!(sigma > 0.f) || !std::isfinite(sigma)) return mfail(SL_EINVAL, "sigma must be > 0");
+  if (M->sigma_set == sigma) return SL_OK;
+  std::vector<float> is(M->R);
+  for (int j = 0; j < M->R; ++j) is[j] = (float)(1.0 / ((double)sigma * M->norms[j]));
+  // pageable source: the copy is staged before the call returns
+  if (cudaMemcpyAsync(M->inv_s, is.data(), M->R * sizeof(float), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return mfail(SL_ECUDA, "uploading 1/s");
+  M->sigma_set = sigma;
+  return SL_OK;
+}
+
+extern "C" {
+
+const char* sl_mlp_last_error(void) { return g_mlp_err.c_str(); }
+
+sl_status sl_mlp_create(const sl_bank* bank, sl_mlp** out) {
+  if (!bank || !out) return mfail(SL_EINVAL, "bank or out is NULL");
+  *out = nullptr;
+  int ndim = 0, R = 0, J = 0;
+  int64_t dims[3];
+  if (sl_bank_info(bank, &ndim, dims, &R, &J) != SL_OK) return mfail(SL_EINVAL, "bad bank");
+  sl_mlp* M = new sl_mlp();
+  M->bank = bank;
+  M->ndim = ndim;
+  M->R = R;
+  M->norms.resize(R);
+  sl_bank_norms(bank, M->norms.data(), nullptr, nullptr);
+  int64_t N = 1;
+  for (int i = 0; i < 3; ++i) {
+    M->geo.dims[i] = i < ndim ? (int)dims[i] : 1;
+    M->geo.lg[i] = lg2(M->geo.dims[i]);
+    N *= M->geo.dims[i];
+  }
+  M->geo.N = N;
+  M->P = n_params(ndim, R);
+  bool ok = cudaMalloc(&M->prm, M->P * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->grad, M->P * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->m, M->P * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->v, M->P * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->loss, sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->inv_s, R * sizeof(float)) == cudaSuccess;
+  if (ok) ok = cudaMemset(M->prm, 0, M->P * sizeof(float)) == cudaSuccess &&
+               cudaMemset(M->m, 0, M->P * sizeof(float)) == cudaSuccess &&
+               cudaMemset(M->v, 0, M->P * sizeof(float)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sl_mlp_free(M);
+    return mfail(SL_ENOMEM, "allocating the MLP");
+  }
+  *out = M;
+  return SL_OK;
+}
+
+void sl_mlp_free(sl_mlp* M) {
+  if (!M) return;
+  cudaFree(M->prm);
+  cudaFree(M->grad);
+  cudaFree(M->m);
+  cudaFree(M->v);
+  cudaFree(M->loss);
+  cudaFree(M->inv_s);
+  cudaFree(M->coeffs);
+  delete M;
+}
+
+int sl_mlp_num_params(const sl_mlp* M) { return M ? M->P : 0; }
+
+sl_status sl_mlp_set_params(sl_mlp* M, const float* host) {
+  if (!M || !host) return mfail(SL_EINVAL, "NULL argument");
+  if (cudaMemcpy(M->prm, host, M->P * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return mfail(SL_ECUDA, "cudaMemcpy");
+  cudaMemset(M->m, 0, M->P * sizeof(float));
+  cudaMemset(M->v, 0, M->P * sizeof(float));
+  M->t = 0;
+  return SL_OK;
+}
+
+sl_status sl_mlp_get_params(const sl_mlp* M, float* host) {
+  if (!M || !host) return mfail(SL_EINVAL, "NULL argument");
+  if (cudaMemcpy(host, M->prm, M->P * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mfail(SL_ECUDA, "cudaMemcpy");
+  return SL_OK;
+}
+
+static sl_status train_launch(sl_mlp* M, const float* noisy, const float* clean, float sigma,
+                              const int* idx, int n, cudaStream_t st) {
+  if (!M || !noisy || !clean || !idx) return mfail(SL_EINVAL, "NULL argument");
+  if (n <= 0 || n % ROWS) return mfail(SL_EINVAL, "n must be a positive multiple of 128");
+  sl_status s = set_sigma(M, sigma, st);
+  if (s != SL_OK) return s;
+  if (cudaMemsetAsync(M->grad, 0, M->P * sizeof(float), st) != cudaSuccess ||
+      cudaMemsetAsync(M->loss, 0, sizeof(float), st) != cudaSuccess)
+    return mfail(SL_ECUDA, "memset");
+  MlpArgs a{};
+  a.prm = M->prm;
+  a.C = noisy;
+  a.Cc = clean;
+  a.idx = idx;
+  a.n = n;
+  a.inv_s = M->inv_s;
+  a.grad = M->grad;
+  a.loss = M->loss;
+  a.geo = M->geo;
+  a.R = M->R;
+  const int tiles = n / ROWS;
+  const int grid = std::min(tiles, 4 * 148);
+  if (M->ndim == 2) {
+    const size_t sm = train_smem<2>();
+    cudaFuncSetAttribute(k_mlp_train<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mlp_train<2><<<grid, 32 * WARPS, sm, st>>>(a);
+  } else {
+    const size_t sm = train_smem<3>();
+    cudaFuncSetAttribute(k_mlp_train<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mlp_train<3><<<grid, 32 * WARPS, sm, st>>>(a);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_mlp_train: ") + cudaGetErrorString(e));
+  return SL_OK;
+}
+
+sl_status sl_mlp_gradients(sl_mlp* M, const float* noisy, const float* clean, float sigma,
+                           const int* idx, int n, float* grad_host, float* loss_host,
+                           void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  sl_status s = train_launch(M, noisy, clean, sigma, idx, n, st);
+  if (s != SL_OK) return s;
+  if (grad_host && cudaMemcpyAsync(grad_host, M->grad, M->P * sizeof(float),
+                                   cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return mfail(SL_ECUDA, "copy gradients");
+  if (loss_host &&
+      cudaMemcpyAsync(loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return mfail(SL_ECUDA, "copy loss");
+  if (cudaStreamSynchronize(st) != cudaSuccess) return mfail(SL_ECUDA, "synchronize");
+  return SL_OK;
+}
+
+sl_status sl_mlp_train_step(sl_mlp* M, const float* noisy, const float* clean, float sigma,
+                            const int* idx, int n, float lr, float* loss_dev, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  sl_status s = train_launch(M, noisy, clean, sigma, idx, n, st);
+  if (s != SL_OK) return s;
+  M->t += 1;
+  const float c1 = 1.f - std::pow(0.9f, (float)M->t), c2 = 1.f - std::pow(0.999f, (float)M->t);
+  k_adam<<<(M->P + 255) / 256, 256, 0, st>>>(M->prm, M->grad, M->m, M->v, M->P, lr, c1, c2);
+  if (loss_dev &&
+      cudaMemcpyAsync(loss_dev, M->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return mfail(SL_ECUDA, "copy loss");
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_adam: ") + cudaGetErrorString(e));
+  return SL_OK;
+}
+
+sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, void* stream) {
+  if (!M || !coeffs || !out) return mfail(SL_EINVAL, "NULL argument");
+  if (out == coeffs) return mfail(SL_EINVAL, "out must not alias coeffs (features read neighbours)");
+  cudaStream_t st = (cudaStream_t)stream;
+  sl_status s = set_sigma(M, sigma, st);
+  if (s != SL_OK) return s;
+  MlpArgs a{};
+  a.prm = M->prm;
+  a.C = coeffs;
+  a.out = out;
+  a.inv_s = M->inv_s;
+  a.geo = M->geo;
+  a.R = M->R;
+  const int grid = 4 * 148;
+  if (M->ndim == 2) {
+    const size_t sm = apply_smem<2>();
+    cudaFuncSetAttribute(k_mlp_apply<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mlp_apply<2><<<grid, 32 * WARPS, sm, st>>>(a);
+  } else {
+    const size_t sm = apply_smem<3>();
+    cudaFuncSetAttribute(k_mlp_apply<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mlp_apply<3><<<grid, 32 * WARPS, sm, st>>>(a);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_mlp_apply: ") + cudaGetErrorString(e));
+  return SL_OK;
+}
+
+sl_status sl_mlp_denoise(sl_mlp* M, const float* noisy, float* out, float sigma, void* stream) {
+  if (!M || !noisy || !out) return mfail(SL_EINVAL, "NULL argument");
+  if (!M->coeffs &&
+      cudaMalloc(&M->coeffs, 2 * (size_t)M->R * M->geo.N * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return mfail(SL_ENOMEM, "coefficient buffer");
+  }
+  sl_status s = sl_forward(M->bank, noisy, M->coeffs, stream);
+  if (s != SL_OK) return mfail(s, std::string("sl_forward: ") + sl_last_error());
+  float* shrunk = M->coeffs + (size_t)M->R * M->geo.N;
+  s = sl_mlp_apply(M, M->coeffs, shrunk, sigma, stream);
+  if (s != SL_OK) return s;
+  s = sl_inverse(M->bank, shrunk, out, stream);
+  if (s != SL_OK) return mfail(s, std::string("sl_inverse: ") + sl_last_error());
+  return SL_OK;
+}
+
+}  // extern "C"

@@ -51,6 +51,18 @@ SIGNATURES = {
     "sl_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _c_float_p, _vp]),
     "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sl_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sl_mlp_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "sl_mlp_free": (None, [_vp]),
+    "sl_mlp_num_params": (ctypes.c_int, [_vp]),
+    "sl_mlp_set_params": (ctypes.c_int, [_vp, _c_float_p]),
+    "sl_mlp_get_params": (ctypes.c_int, [_vp, _c_float_p]),
+    "sl_mlp_gradients": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp, ctypes.c_int,
+                                        _c_float_p, _c_float_p, _vp]),
+    "sl_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp, ctypes.c_int,
+                                         ctypes.c_float, _vp, _vp]),
+    "sl_mlp_apply": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp]),
+    "sl_mlp_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp]),
+    "sl_mlp_last_error": (ctypes.c_char_p, []),
     "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sl_profile_reset": (ctypes.c_int, []),
     "sl_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), _c_int64_p,
@@ -320,3 +332,84 @@ class Bank:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------- learned shrinkage ---
+
+def _mcheck(status: int, where: str) -> None:
+    if status != SL_OK:
+        raise ShearletError(status, where, lib().sl_mlp_last_error().decode(errors="replace"))
+
+
+class MLP:
+    """Learned shrinkage bound to a device Bank (sl_mlp_*)."""
+
+    def __init__(self, bank: "Bank"):
+        self.bank = bank
+        h = _vp()
+        _mcheck(lib().sl_mlp_create(bank.handle, ctypes.byref(h)), "sl_mlp_create")
+        self.handle = h.value
+        self.num_params = lib().sl_mlp_num_params(self.handle)
+
+    def set_params(self, flat: np.ndarray) -> None:
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.num_params
+        _mcheck(lib().sl_mlp_set_params(self.handle, flat.ctypes.data_as(_c_float_p)),
+                "sl_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _mcheck(lib().sl_mlp_get_params(self.handle, out.ctypes.data_as(_c_float_p)),
+                "sl_mlp_get_params")
+        return out
+
+    def _sample(self, idx):
+        import torch
+        if idx.dtype != torch.int32 or not idx.is_cuda or not idx.is_contiguous():
+            raise TypeError("idx must be a contiguous int32 CUDA tensor")
+        return idx.data_ptr(), idx.numel()
+
+    def gradients(self, noisy, clean, sigma: float, idx, stream=None):
+        n_all = self.bank.R * self.bank.N
+        ip, n = self._sample(idx)
+        g = np.zeros(self.num_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _mcheck(lib().sl_mlp_gradients(self.handle, _dev_ptr(noisy, "noisy", n_all),
+                                       _dev_ptr(clean, "clean", n_all), float(sigma), ip, n,
+                                       g.ctypes.data_as(_c_float_p), ctypes.byref(loss),
+                                       _stream_ptr(stream)), "sl_mlp_gradients")
+        return float(loss.value), g
+
+    def train_step(self, noisy, clean, sigma: float, idx, lr: float, loss_out=None, stream=None):
+        n_all = self.bank.R * self.bank.N
+        ip, n = self._sample(idx)
+        lp = None if loss_out is None else loss_out.data_ptr()
+        _mcheck(lib().sl_mlp_train_step(self.handle, _dev_ptr(noisy, "noisy", n_all),
+                                        _dev_ptr(clean, "clean", n_all), float(sigma), ip, n,
+                                        float(lr), lp, _stream_ptr(stream)), "sl_mlp_train_step")
+
+    def apply(self, coeffs, sigma: float, out=None, stream=None):
+        n_all = self.bank.R * self.bank.N
+        out = self.bank._empty((self.bank.R,) + self.bank.dims) if out is None else out
+        _mcheck(lib().sl_mlp_apply(self.handle, _dev_ptr(coeffs, "coeffs", n_all),
+                                   _dev_ptr(out, "out", n_all), float(sigma),
+                                   _stream_ptr(stream)), "sl_mlp_apply")
+        return out
+
+    def denoise(self, noisy, sigma: float, out=None, stream=None):
+        out = self.bank._empty(self.bank.dims) if out is None else out
+        _mcheck(lib().sl_mlp_denoise(self.handle, _dev_ptr(noisy, "noisy", self.bank.N),
+                                     _dev_ptr(out, "out", self.bank.N), float(sigma),
+                                     _stream_ptr(stream)), "sl_mlp_denoise")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sl_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

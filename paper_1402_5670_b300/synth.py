@@ -105,3 +105,18 @@ def uneven_batch_shapes(n: int, sides: Sequence[int], seed: int) -> List[Tuple[i
     r = _rng(seed)
     s = np.asarray(list(sides))
     return [(int(r.choice(s)), int(r.choice(s))) for _ in range(n)]
+
+
+def mlp_init(ndim: int, R: int, seed: int) -> np.ndarray:
+    """Seeded initial parameters of the learned-shrinkage MLP (flat float32 in the
+    library's layout W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3, E[R][8] with
+    F = 1 + 3^ndim + 8): uniform fan-in scaling for the weights, zero hidden biases,
+    b3 = 2 (the initial gain sigmoid(2) ~ 0.88 keeps most of each coefficient) and a
+    small random subband embedding."""
+    r = _rng(seed)
+    F = 1 + 3 ** ndim + 8
+    parts = [r.uniform(-1, 1, (64, F)) / np.sqrt(F), np.zeros(64),
+             r.uniform(-1, 1, (64, 64)) / 8.0, np.zeros(64),
+             r.uniform(-1, 1, 64) / 8.0, np.array([2.0]),
+             0.1 * r.standard_normal((R, 8))]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)

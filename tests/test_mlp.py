@@ -1,0 +1,203 @@
+"""Learned shrinkage: the FP64 oracle against finite differences (CPU), and the GPU
+training and inference kernels against the oracle (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from oracle import shearlet_oracle as O
+from paper_1402_5670_b300 import synth
+from tests.conftest import oracle_system
+
+
+def _random_problem(ndim, seed=0):
+    dims = (16, 16) if ndim == 2 else (8, 8, 8)
+    R = 7
+    r = np.random.default_rng(seed)
+    C = r.standard_normal((R,) + dims) * 3.0
+    Cc = C * (np.abs(C) > 2.0)
+    s = r.uniform(0.5, 2.0, R)
+    n = 40
+    j = r.integers(1, R, n)
+    m = np.stack([r.integers(0, d, n) for d in dims], 1)
+    p = M.unflatten(synth.mlp_init(ndim, R, seed).astype(np.float64), ndim, R)
+    p["b1"] = r.standard_normal(64) * 0.1
+    p["b2"] = r.standard_normal(64) * 0.1
+    return p, C, Cc, s, j, m
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_oracle_gradients_match_finite_differences(ndim):
+    """The analytic backward pass of the oracle equals central differences of its loss
+    (FP64), for every parameter tensor including the subband embedding, which enters
+    through the features."""
+    p, C, Cc, s, j, m = _random_problem(ndim)
+    c = C[(j,) + tuple(m.T)]
+    cc = Cc[(j,) + tuple(m.T)]
+
+    def loss_of(pp):
+        return M.loss(pp, M.features(C, j, m, s, pp["E"]), c, cc, s[j])
+
+    L, g = M.backward(p, M.features(C, j, m, s, p["E"]), c, cc, s[j], j)
+    assert abs(loss_of(p) - L) < 1e-12
+    r = np.random.default_rng(1)
+    h = 1e-6
+    for k in M.ORDER:
+        flat = p[k].ravel()
+        for i in r.choice(flat.size, min(6, flat.size), replace=False):
+            q = {kk: vv.copy() for kk, vv in p.items()}
+            q[k].ravel()[i] += h
+            Lp = loss_of(q)
+            q[k].ravel()[i] -= 2 * h
+            Lm = loss_of(q)
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g[k].ravel()[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (k, i)
+
+
+def test_pin_catches_wrong_relu_derivative():
+    """Planted mistake: the ReLU derivative taken as 1 everywhere (gradient flowing
+    through inactive units). Finite differences of the loss separate it from the
+    oracle's gradient."""
+    p, C, Cc, s, j, m = _random_problem(2)
+    c = C[(j,) + tuple(m.T)]
+    cc = Cc[(j,) + tuple(m.T)]
+    X = M.features(C, j, m, s, p["E"])
+    L, g = M.backward(p, X, c, cc, s[j], j)
+    gv, _ = M.forward(p, X)
+    dz3 = 2 * (gv * c - cc) / s[j] * c / s[j] / len(c) * gv * (1 - gv)
+    wrong_b2 = np.outer(dz3, p["w3"]).sum(0)
+    h = 1e-6
+    fd = np.zeros(64)
+    for i in range(64):
+        q = {kk: vv.copy() for kk, vv in p.items()}
+        q["b2"][i] += h
+        Lp = M.loss(q, X, c, cc, s[j])
+        q["b2"][i] -= 2 * h
+        fd[i] = (Lp - M.loss(q, X, c, cc, s[j])) / (2 * h)
+    assert np.max(np.abs(g["b2"] - fd)) < 1e-8
+    assert np.max(np.abs(wrong_b2 - fd)) > 1e-6
+
+
+def test_features_neighbourhood_order():
+    """x_1..x_9 are |C| over the 3x3 neighbourhood in row-major order with periodic
+    wrap, scaled by 1/s; x_0 is the signed centre."""
+    C = np.zeros((2, 4, 5))
+    C[1] = np.arange(20).reshape(4, 5) - 7.0
+    E = np.zeros((2, 8))
+    X = M.features(C, np.array([1]), np.array([[0, 0]]), np.array([1.0, 2.0]), E)
+    want = [C[1, 0, 0] / 2] + [abs(C[1, a % 4, b % 5]) / 2 for a in (-1, 0, 1) for b in (-1, 0, 1)]
+    assert np.allclose(X[0, :10], want)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 3.14159])
+    assert list(M.bf16(v)) == [1.0, 1.0, 1.0 + 2 ** -6, -2.5, 3.140625]
+
+
+# ------------------------------------------------------------------- GPU ---
+
+torch = pytest.importorskip("torch")
+
+
+def _gpu_setup(dims, J, sl, seed):
+    from paper_1402_5670_b300.build import build
+    from paper_1402_5670_b300.shearlet import MLP, Bank
+    build()
+    b = Bank(dims, J, sl, device=0)
+    clean = (synth.piecewise_smooth_image(dims, seed) if len(dims) == 2
+             else synth.moving_ellipses_volume(dims, seed))
+    noisy = synth.add_noise(clean, 20.0, seed + 1)
+    Cn = b.forward(torch.from_numpy(noisy).cuda())
+    Cc = b.forward(torch.from_numpy(clean).cuda())
+    mlp = MLP(b)
+    flat = synth.mlp_init(len(dims), b.R, seed + 2)
+    mlp.set_params(flat)
+    return b, mlp, flat, Cn, Cc
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", [((64, 64), 2, (1, 1)), ((16, 16, 16), 1, (0,))], ids=str)
+def test_gpu_gradients_match_oracle(case):
+    """The tensor-core backward pass against the oracle: within 1e-2 of the oracle with
+    the same BF16 operand rounding (FP32 vs FP64 accumulation, rare rounding-boundary
+    flips), and within 5e-2 of the exact FP64 gradients (the BF16 effect itself)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dims, J, sl = case
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 3)
+    s_sys = oracle_system(dims, J, sl)
+    r = np.random.default_rng(5)
+    n = 2048
+    q = r.integers(b.N, b.R * b.N, n)
+    idx = torch.from_numpy(q.astype(np.int32)).cuda()
+    sigma = 20.0
+    L_gpu, g_gpu = mlp.gradients(Cn, Cc, sigma, idx)
+    C = Cn.cpu().numpy().astype(np.float64)
+    CC = Cc.cpu().numpy().astype(np.float64)
+    j = q // b.N
+    m = np.stack(np.unravel_index(q % b.N, dims), 1)
+    s = sigma * s_sys.norms
+    p = M.unflatten(flat.astype(np.float64), len(dims), b.R)
+    X = M.features(C, j, m, s, p["E"])
+    c = C[(j,) + tuple(m.T)]
+    cc = CC[(j,) + tuple(m.T)]
+    L_q, g_q = M.backward(p, X, c, cc, s[j], j, bf16_operands=True)
+    L_x, g_x = M.backward(p, X, c, cc, s[j], j)
+    gq, gx = M.flatten(g_q), M.flatten(g_x)
+    assert abs(L_gpu - L_q) <= 1e-3 * L_q
+    off = 0
+    for k, sh in M.param_shapes(len(dims), b.R).items():
+        sz = int(np.prod(sh))
+        e1 = _rel(g_gpu[off:off + sz], gq[off:off + sz])
+        e2 = _rel(g_gpu[off:off + sz], gx[off:off + sz])
+        assert e1 < 1e-2, (k, e1)
+        assert e2 < 5e-2, (k, e2)
+        off += sz
+
+
+@pytest.mark.gpu
+def test_gpu_apply_matches_oracle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dims, J, sl = (64, 64), 2, (1, 1)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 4)
+    s_sys = oracle_system(dims, J, sl)
+    out = mlp.apply(Cn, 20.0).cpu().numpy()
+    p = M.unflatten(flat.astype(np.float64), 2, b.R)
+    ref = M.apply(p, Cn.cpu().numpy().astype(np.float64), 20.0 * s_sys.norms, bf16_operands=True)
+    assert np.array_equal(out[0], Cn[0].cpu().numpy())
+    assert np.max(np.abs(out - ref)) <= 2e-3 * np.max(np.abs(ref))
+
+
+@pytest.mark.gpu
+def test_learned_shrinkage_beats_hard_thresholding():
+    """Trained on the GPU from transform-generated pairs, the learned gain must denoise
+    held-out synthetic images better (PSNR) than the paper's hard threshold at every
+    tested noise level."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5670_b300 import learned
+    from paper_1402_5670_b300.shearlet import MLP, Bank
+    dims, J, sl = (256, 256), 2, (1, 1)
+    b = Bank(dims, J, sl, device=0)
+    mlp = MLP(b)
+    mlp.set_params(synth.mlp_init(2, b.R, 11))
+    pairs = learned.make_pairs(b, [10.0, 20.0, 30.0, 40.0], seeds=[100, 101, 102, 103, 104, 105])
+    hist = learned.train(mlp, pairs, steps=6000, batch=32768, lr=3e-3, seed=1)
+    assert hist[-1] < hist[0]
+    K = [2.5, 3.8]
+    gains = []
+    for sg in (10.0, 20.0, 30.0, 40.0):
+        for sd in (500, 501):
+            clean = synth.piecewise_smooth_image(dims, sd)
+            noisy = synth.add_noise(clean, sg, sd + 9)
+            xg = torch.from_numpy(noisy).cuda()
+            hard = b.denoise(xg, sg, K).cpu().numpy()
+            lrn = mlp.denoise(xg, sg).cpu().numpy()
+            gains.append(O.psnr(clean, lrn) - O.psnr(clean, hard))
+    print("PSNR gain of learned over hard thresholding (dB):", np.round(gains, 2))
+    assert min(gains) > 0.0
+    assert float(np.mean(gains)) > 0.1
