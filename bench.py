@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the secondary measurements (denoise, threshold, MLP, 3D)")
     p.add_argument("--path", choices=["auto", "general", "cluster"], default="auto",
                    help="kernel path of the library (auto: the one measured faster)")
     return p.parse_args()
@@ -295,12 +297,109 @@ def run_ours(args):
                 "api": "sl_fwdinv_host (pinned host buffers)"},
         "clocks": clk,
     }
+    if n_gpus == 1 and not args.no_extras:
+        line["extras"] = extras(b, x, clean, C, flush, args)
     if n_gpus == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=12.0)
     print(json.dumps(line))
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------ secondary measurements ---
+
+def _time_graph(fn, flush, steps: int) -> float:
+    """Mean device time (ms) of fn captured in a CUDA graph, L2 flushed between runs."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(3):
+        flush.zero_()
+        g.replay()
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(st)
+        g.replay()
+        b.record(st)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def extras(b, x, clean, C, flush, args):
+    """Throughput of the other hot-path operations on the same workload (and the 3D
+    configuration): fused hard-threshold denoising, the standalone threshold, the
+    learned shrinkage (training step and inference), GPU error statistics, and the
+    128^3 volume transform."""
+    import torch
+    from paper_1402_5670_b300 import learned, synth
+    from paper_1402_5670_b300.shearlet import MLP, Bank, sl_error_stats
+    peak, _ = peaks()
+    steps = max(5, min(args.steps, 30))
+    R, N, Nh = b.R, b.N, b.Nh
+    out = {}
+    K = [2.5, 2.5, 2.5, 3.8]
+    y = torch.empty_like(x)
+    ms = _time_graph(lambda: b.denoise(x, SIGMA, K, out=y), flush, steps)
+    cl = torch.from_numpy(clean).cuda()
+    alg = 4 * R * Nh + 8 * Nh + 8 * N
+    out["denoise_hard_fused"] = {
+        "ms": ms, "images_per_s": 1e3 / ms, "coeffs_per_s": R * N / (ms * 1e-3),
+        "alg_bytes": alg, "frac_hbm": alg / (ms * 1e-3) / 1e9 / peak,
+        "psnr_noisy": sl_error_stats(x, cl)["psnr"], "psnr_denoised": sl_error_stats(y, cl)["psnr"]}
+    Cw = C.clone()
+    ms = _time_graph(lambda: b.threshold_(Cw, SIGMA, K), flush, steps)
+    out["threshold"] = {"ms": ms, "GBps": 8 * (R - 1) * N / (ms * 1e-3) / 1e9,
+                        "frac_hbm": 8 * (R - 1) * N / (ms * 1e-3) / 1e9 / peak}
+    # learned shrinkage
+    mlp = MLP(b)
+    mlp.set_params(synth.mlp_init(2, R, 11))
+    pairs = learned.make_pairs(b, [10.0, 20.0, 30.0, 40.0], seeds=[100, 101])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    batch = 65536
+    idx = (torch.randint(0, (R - 1) * N, (batch,), generator=gen, device="cuda") + N).to(torch.int32)
+    Cn, Cc, sg = pairs[0]
+    ms_t = _time_graph(lambda: mlp.train_step(Cn, Cc, sg, idx, 1e-4), flush, steps)
+    F = 1 + 9 + 8
+    fl_fwd = 2 * (F * 64 + 64 * 64 + 64)
+    learned.train(mlp, pairs, steps=2000, batch=32768, lr=3e-3, seed=1)
+    Ca = torch.empty_like(C)
+    ms_i = _time_graph(lambda: mlp.apply(C, SIGMA, out=Ca), flush, steps)
+    ymlp = mlp.denoise(x, SIGMA)
+    out["mlp_shrinkage"] = {
+        "train_step_ms": ms_t, "train_samples_per_s": batch / (ms_t * 1e-3),
+        "train_tflops": 3 * fl_fwd * batch / (ms_t * 1e-3) / 1e12,
+        "infer_ms": ms_i, "infer_coeffs_per_s": (R - 1) * N / (ms_i * 1e-3),
+        "infer_tflops": fl_fwd * (R - 1) * N / (ms_i * 1e-3) / 1e12,
+        "psnr_learned": sl_error_stats(ymlp, cl)["psnr"],
+        "note": "BF16 mma.sync tensor cores, FP32 accumulate; flops count the two "
+                "dense layers and the output dot (backward ~2x forward)"}
+    # 3D volume, 128^3, three scales, levels (1,1,2): R = 292
+    try:
+        b3 = Bank((128, 128, 128), 3, (1, 1, 2), device=b.device)
+        v = synth.add_noise(synth.moving_ellipses_volume((128, 128, 128), SEED), SIGMA, SEED + 5)
+        xv = torch.from_numpy(v).cuda()
+        C3 = torch.empty((b3.R, 128, 128, 128), device="cuda")
+        y3 = torch.empty_like(xv)
+        ms3 = _time_graph(lambda: (b3.forward(xv, out=C3), b3.inverse(C3, out=y3)), flush,
+                          max(3, steps // 3))
+        alg3 = 8 * b3.N + 8 * b3.R * b3.N + 8 * b3.R * b3.Nh + 8 * b3.Nh
+        out["3d_128_fwd_inv"] = {
+            "ms": ms3, "coeffs_per_s": b3.R * b3.N / (ms3 * 1e-3), "R": b3.R,
+            "alg_bytes": alg3, "frac_hbm": alg3 / (ms3 * 1e-3) / 1e9 / peak,
+            "rel_err_reconstruction": float((y3 - xv).abs().max() / xv.abs().max())}
+        del C3
+        b3.close()
+    except Exception as e:  # report, do not fail the headline line
+        out["3d_128_fwd_inv"] = {"error": str(e)}
+    return out
 
 
 # ----------------------------------------------------- oracle on the host ---

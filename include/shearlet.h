@@ -252,6 +252,17 @@ sl_status sl_mlp_denoise(sl_mlp* mlp, const float* noisy, float* out, float sigm
 const char* sl_mlp_last_error(void);
 
 /*
+ * Error statistics of y against ref (DEVICE float arrays of n elements), accumulated
+ * in FP64 on the GPU: stats[0] = max |y - ref|, stats[1] = max |ref|,
+ * stats[2] = sum (y - ref)^2, stats[3] = sum ref^2 (host array of 4 doubles).
+ * PSNR (eq. PSNR, Sec. 5.3) = 20 log10(255 sqrt(n) / sqrt(stats[2])); the relative
+ * errors of the parity tests are stats[0] / stats[1] and sqrt(stats[2] / stats[3]).
+ * Synchronises the stream.
+ */
+sl_status sl_error_stats(const float* y, const float* ref, int64_t n, double* stats,
+                         void* stream);
+
+/*
  * Kernel timing for profiling. When enabled, every kernel launch of the library is
  * bracketed by CUDA events recorded on the launch stream; sl_profile_read returns,
  * per kernel kind, the number of launches, their summed device time (ms) and their

@@ -724,6 +724,51 @@ constexpr int col_inv_pipe_smem_bytes() {
 
 // ------------------------------------------------------------ elementwise ---
 
+// Error statistics of y against ref over n elements, accumulated in FP64:
+// acc[0] = max |y - ref|, acc[1] = max |ref|, acc[2] = sum (y - ref)^2, acc[3] = sum ref^2.
+// Maxima of non-negative doubles are ordered like their bit patterns.
+__global__ void __launch_bounds__(256) k_error_stats(const float* __restrict__ y,
+                                                     const float* __restrict__ ref, int64_t n,
+                                                     double* __restrict__ acc) {
+  double me = 0.0, mr = 0.0, se = 0.0, sr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = ref[i], e = (double)y[i] - r;
+    me = fmax(me, fabs(e));
+    mr = fmax(mr, fabs(r));
+    se += e * e;
+    sr += r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    me = fmax(me, __shfl_xor_sync(0xffffffffu, me, o));
+    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+  __shared__ double red[4][8];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = me;
+    red[1][w] = mr;
+    red[2][w] = se;
+    red[3][w] = sr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      me = fmax(me, red[0][k]);
+      mr = fmax(mr, red[1][k]);
+      se += red[2][k];
+      sr += red[3][k];
+    }
+    atomicMax(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)__double_as_longlong(me));
+    atomicMax(reinterpret_cast<unsigned long long*>(acc + 1),
+              (unsigned long long)__double_as_longlong(mr));
+    atomicAdd(acc + 2, se);
+    atomicAdd(acc + 3, sr);
+  }
+}
+
 // In-place hard threshold of nf consecutive coefficient arrays of n elements each.
 __global__ void __launch_bounds__(256) k_threshold(float* c, int64_t n, int nf, Thresholds thr) {
   const int f = blockIdx.y;

@@ -1160,6 +1160,24 @@ sl_status sl_fwdinv_host(const sl_bank* cb, const float* x_host, float* y_host, 
   return SL_OK;
 }
 
+sl_status sl_error_stats(const float* y, const float* ref, int64_t n, double* stats,
+                         void* stream) {
+  if (!y || !ref || !stats || n <= 0) return fail(SL_EINVAL, "NULL argument or n <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* acc = nullptr;
+  SL_CUDA(cudaMallocAsync((void**)&acc, 4 * sizeof(double), st));
+  SL_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), st));
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * 148);
+  sl::dev::k_error_stats<<<grid, 256, 0, st>>>(y, ref, n, acc);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(stats, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(acc, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sl_error_stats");
+  return SL_OK;
+}
+
 sl_status sl_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof_on = on != 0;

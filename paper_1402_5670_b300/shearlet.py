@@ -63,6 +63,7 @@ SIGNATURES = {
     "sl_mlp_apply": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp]),
     "sl_mlp_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp]),
     "sl_mlp_last_error": (ctypes.c_char_p, []),
+    "sl_error_stats": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _c_double_p, _vp]),
     "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sl_profile_reset": (ctypes.c_int, []),
     "sl_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), _c_int64_p,
@@ -183,6 +184,22 @@ def sl_forward_noalloc(bank: int, psi, x, coeffs, stream=None) -> None:
     """Forward transform that allocates nothing (static device scratch); psi, x and
     coeffs are device pointers owned by the caller."""
     _check(lib().sl_forward_noalloc(bank, psi, x, coeffs, stream), "sl_forward_noalloc")
+
+
+def sl_error_stats(y, ref, stream=None) -> dict:
+    """GPU error statistics (FP64 accumulation) of device tensors y against ref:
+    max_abs_err, max_abs_ref, sum_sq_err, sum_sq_ref, and the derived rel_max, rel_l2
+    and psnr (peak 255, eq. PSNR)."""
+    n = ref.numel()
+    out = np.zeros(4)
+    _check(lib().sl_error_stats(_dev_ptr(y, "y", n), _dev_ptr(ref, "ref", n), n,
+                                out.ctypes.data_as(_c_double_p), _stream_ptr(stream)),
+           "sl_error_stats")
+    import math
+    return {"max_abs_err": out[0], "max_abs_ref": out[1], "sum_sq_err": out[2],
+            "sum_sq_ref": out[3], "rel_max": out[0] / max(out[1], 1e-300),
+            "rel_l2": math.sqrt(out[2] / max(out[3], 1e-300)),
+            "psnr": 20 * math.log10(255 * math.sqrt(n) / math.sqrt(max(out[2], 1e-300)))}
 
 
 def sl_profile_enable(on: bool) -> None:

@@ -247,3 +247,16 @@ def test_full_size_3d_128():
         assert np.max(np.abs(got - ref)) / scale < TOL
     xi = b.inverse(C).cpu().numpy()
     assert rel(xi, x) < TOL
+
+
+def test_error_stats_kernel_matches_numpy():
+    """The FP64-accumulating GPU reduction (max and L2 errors, PSNR of eq. PSNR)."""
+    from paper_1402_5670_b300.shearlet import sl_error_stats
+    x = synth.piecewise_smooth_image((512, 512), 3)
+    y = synth.add_noise(x, 25.0, 4)
+    st = sl_error_stats(cuda(y), cuda(x))
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    assert st["max_abs_err"] == np.max(np.abs(yd - xd))
+    assert st["max_abs_ref"] == np.max(np.abs(xd))
+    assert abs(st["sum_sq_err"] - np.sum((yd - xd) ** 2)) <= 1e-12 * np.sum((yd - xd) ** 2)
+    assert abs(st["psnr"] - O.psnr(xd, yd)) < 1e-9
