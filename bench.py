@@ -381,6 +381,10 @@ def extras(b, x, clean, C, flush, args):
         "psnr_learned": sl_error_stats(ymlp, cl)["psnr"],
         "note": "BF16 mma.sync tensor cores, FP32 accumulate; flops count the two "
                 "dense layers and the output dot (backward ~2x forward)"}
+    try:
+        out["batched_uneven_64"] = batched_uneven(flush, steps, peak)
+    except Exception as e:  # report, do not fail the headline line
+        out["batched_uneven_64"] = {"error": str(e)}
     # 3D volume, 128^3, three scales, levels (1,1,2): R = 292
     try:
         b3 = Bank((128, 128, 128), 3, (1, 1, 2), device=b.device)
@@ -400,6 +404,63 @@ def extras(b, x, clean, C, flush, args):
     except Exception as e:  # report, do not fail the headline line
         out["3d_128_fwd_inv"] = {"error": str(e)}
     return out
+
+
+def batched_uneven(flush, steps: int, peak: float) -> dict:
+    """64 seeded images with sides drawn from {256, 384, 512, 1024}, four scales,
+    levels (1,1,2,2): forward + inverse of the whole batch as one graph launch (after
+    the autotuner has picked the group caps and the branch count), against the same
+    images transformed one after another (single-image calls, graph captured)."""
+    import torch
+    from paper_1402_5670_b300 import synth
+    from paper_1402_5670_b300.shearlet import Bank, Batch
+    shapes = synth.uneven_batch_shapes(64, (256, 384, 512, 1024), SEED)
+    cache = {}
+    for d in shapes:
+        if d not in cache:
+            cache[d] = Bank(d, J, LEVELS, device=torch.cuda.current_device())
+    banks = [cache[d] for d in shapes]
+    xs = [torch.from_numpy(synth.add_noise(synth.piecewise_smooth_image(d, SEED + i), SIGMA,
+                                           SEED + 500 + i)).cuda() for i, d in enumerate(shapes)]
+    cs = [torch.empty((b.R,) + b.dims, device="cuda") for b in banks]
+    ys = [torch.empty_like(x) for x in xs]
+    coeffs = sum(b.R * b.N for b in banks)
+    alg = sum(8 * b.N + 8 * b.R * b.N + 8 * b.R * b.Nh + 8 * b.Nh for b in banks)
+    B = Batch(banks)
+    tune_ms = B.autotune(xs, cs, ys, reps=3)
+    info = B.info()
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        B.fwdinv(xs, cs, ys)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, e in ev:
+        flush.zero_()
+        a.record(st)
+        B.fwdinv(xs, cs, ys)
+        e.record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    err = max(float((y - x).abs().max() / x.abs().max()) for x, y in zip(xs, ys))
+
+    def sequential():
+        for b, x, c, y in zip(banks, xs, cs, ys):
+            b.forward(x, out=c)
+            b.inverse(c, out=y)
+
+    ms_seq = _time_graph(sequential, flush, max(3, steps // 3))
+    caps = {f"{d[0]}x{d[1]}": info["group_cap"][shapes.index(d)] for d in cache}
+    res = {"ms": ms, "images": len(shapes), "distinct_shapes": len(cache),
+           "coeffs_per_s": coeffs / (ms * 1e-3), "alg_bytes": alg,
+           "frac_hbm": alg / (ms * 1e-3) / 1e9 / peak, "rel_err_reconstruction": err,
+           "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms,
+           "autotune": {"branches": info["branches"], "group_cap": caps, "best_ms": tune_ms},
+           "launch": "one cudaGraphLaunch per batch (library-captured fork/join graph)"}
+    B.close()
+    del cs
+    for b in cache.values():
+        b.close()
+    return res
 
 
 # ----------------------------------------------------- oracle on the host ---

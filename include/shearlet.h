@@ -61,7 +61,8 @@ const char* sl_last_error(void);
  * Build the digital shearlet filter bank on an N-grid, once (Algorithm 1 prologue;
  * Sec. 4.3 "SLgetShearletSystem2D").
  *   ndim         2 or 3.
- *   dims         ndim sizes (host array), each a power of two in [8, 1024].
+ *   dims         ndim sizes (host array), each a power of two in [8, 1024]; in 2D a
+ *                side may also be 384 = 3 * 2^7 (mixed radix-3/radix-2 line FFTs).
  *   nScales      number of scales J >= 1 (Sec. 4.1 'nScales').
  *   shearLevels  J entries d_j in [0, 4] (host array), coarse to fine (Sec. 4.1
  *                'shearLevels'); scale j then has 2^(d_j+2) filters in 2D and
@@ -175,6 +176,82 @@ sl_status sl_denoise(const sl_bank* bank, const float* noisy, float* out, float 
  */
 sl_status sl_fwdinv_host(const sl_bank* bank, const float* x_host, float* y_host,
                          void* stream);
+
+/* ---------------------------------------------------------------- batches ---
+ * A batch transforms n images at once, image i with bank banks[i]; the banks may
+ * have different shapes (e.g. sides 256, 384, 512 and 1024 in one batch), and
+ * images that share a shape share one bank. The paper transforms one signal per
+ * call (Algorithms 1 and 2); a batch runs the same per-image computation, with
+ * results identical bit for bit to one sl_forward / sl_inverse / sl_denoise per
+ * image.
+ * Execution: the images are spread over K branches (largest estimated cost first,
+ * onto the least loaded branch); every branch owns a workspace and a stream, and
+ * runs its images in turn. The fork and join are captured into one CUDA graph the
+ * first time a call is made with a given set of data pointers (and, for denoise,
+ * thresholds); later calls with the same pointers replay it with one graph launch.
+ * New pointers trigger a new capture (about a millisecond of host time).
+ * Arrays of pointers (x, coeffs, y, K) are HOST arrays of n entries; the pointers
+ * in them are device pointers (K[i]: host array of nScales floats) on the batch's
+ * device. A batch is not reentrant: issue its calls on one stream or serialise
+ * them. Its memory: one workspace per branch, sized for the largest image of that
+ * branch (spectrum, one filter group, partial sums; tens of MB for 1024^2).
+ */
+typedef struct sl_batch sl_batch; /* opaque; owned by the library */
+
+typedef struct {
+  int branches;   /* concurrent branches K; 0 = default (4), clamped to n */
+  int no_graph;   /* 1: issue kernels directly instead of capturing a graph */
+  int reserved[6];
+} sl_batch_options;
+
+/* Create a batch over banks[0..n) (all built on the current device, any path).
+ * opt may be NULL. SL_EINVAL for NULL/invalid arguments or a host-only bank,
+ * SL_ENOMEM if the workspaces do not fit. */
+sl_status sl_batch_create(const sl_bank* const* banks, int n, const sl_batch_options* opt,
+                          sl_batch** out);
+
+/* Release the batch (synchronises the device when workspaces are freed). NULL is a no-op. */
+void sl_batch_free(sl_batch* batch);
+
+/* Schedule of the batch: the number of branches, and for every image (arrays of n,
+ * each may be NULL) its branch and the filters-per-group cap its plan uses. */
+sl_status sl_batch_info(const sl_batch* batch, int* branches, int* branch_of, int* group_cap);
+
+/* Forward transform of every image: x[i][dims_i] -> coeffs[i][R_i][dims_i]. */
+sl_status sl_batch_forward(sl_batch* batch, const float* const* x, float* const* coeffs,
+                           void* stream);
+
+/* Dual-frame inverse of every image: coeffs[i] -> x[i]. */
+sl_status sl_batch_inverse(sl_batch* batch, const float* const* coeffs, float* const* x,
+                           void* stream);
+
+/* Forward then inverse of every image (coeffs[i] is written and read back):
+ * x[i] -> coeffs[i] -> y[i]. */
+sl_status sl_batch_fwdinv(sl_batch* batch, const float* const* x, float* const* coeffs,
+                          float* const* y, void* stream);
+
+/* Fused denoise (as sl_denoise) of every image: noisy[i] -> out[i] with thresholds
+ * K[i][s] * sigma * ||psi_j||_2. Needs general-path banks (SL_ENOTSUP otherwise). */
+sl_status sl_batch_denoise(sl_batch* batch, const float* const* noisy, float* const* out,
+                           float sigma, const float* const* K, void* stream);
+
+/* Autotuner. Runs sl_batch_fwdinv-shaped work on the caller's buffers (their
+ * contents are overwritten) and keeps the fastest settings: first, per distinct
+ * bank, the filters-per-group cap (candidates: the bank's default, R, R/2, R/4,
+ * R/8; one image of that shape timed alone); then the number of branches K in
+ * {1, 2, 3, 4, 6, 8, 12, 16} (<= n) for the whole batch, captured as it will run.
+ * Each candidate is timed `reps` times (>= 2; the first call is a warm-up) with CUDA
+ * events on `stream`, keeping the minimum. Synchronous. best_ms (may be NULL)
+ * receives the best batch time. */
+sl_status sl_batch_autotune(sl_batch* batch, const float* const* x, float* const* coeffs,
+                            float* const* y, int reps, void* stream, double* best_ms);
+
+/* One-shot forms: create a batch (no graph, default branches), run it on `stream`,
+ * wait for the stream, free the batch. For repeated calls keep a batch instead. */
+sl_status sl_forward_batch(const sl_bank* const* banks, int n, const float* const* x,
+                           float* const* coeffs, void* stream);
+sl_status sl_inverse_batch(const sl_bank* const* banks, int n, const float* const* coeffs,
+                           float* const* x, void* stream);
 
 /*
  * Allocation-free forward transform. The paper has no counterpart: this entry point

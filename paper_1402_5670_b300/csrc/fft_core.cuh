@@ -50,7 +50,8 @@ constexpr double cx_cos(double x) {
   return s;
 }
 
-// W_N^K = exp(-2 pi i K / N) for 0 <= K < N/2 (angle in (-pi, 0]).
+// W_N^K = exp(-2 pi i K / N) for 0 <= K < 2N/3 (angle in (-4pi/3, 0]; the series
+// error there is still below 1e-23).
 template <int N, int K>
 struct Tw {
   static constexpr float re = (float)cx_cos(-2.0 * kPiD * K / N);
@@ -89,18 +90,65 @@ __device__ __forceinline__ void dft_combine(float2 (&x)[N], const float2 (&e)[N 
   (dft_bfly<N, DIR, K>(x, e, o), ...);
 }
 
+// Radix-3 decimation in time for N divisible by 3:
+//   X[k + r N/3] = E0[k] + w^r W^k E1[k] + w^{2r} W^{2k} E2[k],  w = W_3, W = W_N,
+// with E_m the length-N/3 DFT of x[3n + m].
+template <int N, int DIR, int K>
+__device__ __forceinline__ void dft3_bfly(float2 (&x)[N], const float2 (&e0)[N / 3],
+                                          const float2 (&e1)[N / 3], const float2 (&e2)[N / 3]) {
+  constexpr int M = N / 3;
+  float2 t1 = e1[K], t2 = e2[K];
+  if constexpr (K != 0) {
+    constexpr float c1 = Tw<N, K>::re, s1 = DIR < 0 ? Tw<N, K>::im : -Tw<N, K>::im;
+    constexpr float c2 = Tw<N, 2 * K>::re, s2 = DIR < 0 ? Tw<N, 2 * K>::im : -Tw<N, 2 * K>::im;
+    t1 = make_float2(t1.x * c1 - t1.y * s1, t1.x * s1 + t1.y * c1);
+    t2 = make_float2(t2.x * c2 - t2.y * s2, t2.x * s2 + t2.y * c2);
+  }
+  // w = cos(2pi/3) -+ i sin(2pi/3): t1 w + t2 w^2 and t1 w^2 + t2 w
+  constexpr float h = 0.8660254037844386f;  // sin(2 pi / 3)
+  const float2 sum = cadd(t1, t2), dif = csub(t1, t2);
+  const float2 base = make_float2(e0[K].x - 0.5f * sum.x, e0[K].y - 0.5f * sum.y);
+  // -i h dif for the forward direction (+i h dif for the inverse)
+  const float2 rot = DIR < 0 ? make_float2(h * dif.y, -h * dif.x) : make_float2(-h * dif.y, h * dif.x);
+  x[K] = cadd(e0[K], sum);
+  x[K + M] = cadd(base, rot);
+  x[K + 2 * M] = csub(base, rot);
+}
+
+template <int N, int DIR, int... K>
+__device__ __forceinline__ void dft3_combine(float2 (&x)[N], const float2 (&e0)[N / 3],
+                                             const float2 (&e1)[N / 3], const float2 (&e2)[N / 3],
+                                             std::integer_sequence<int, K...>) {
+  (dft3_bfly<N, DIR, K>(x, e0, e1, e2), ...);
+}
+
 template <int N, int DIR>
 struct Dft {
   static __device__ __forceinline__ void run(float2 (&x)[N]) {
-    float2 e[N / 2], o[N / 2];
+    if constexpr (N % 3 == 0) {
+      constexpr int M = N / 3;
+      float2 e0[M], e1[M], e2[M];
 #pragma unroll
-    for (int i = 0; i < N / 2; ++i) {
-      e[i] = x[2 * i];
-      o[i] = x[2 * i + 1];
+      for (int i = 0; i < M; ++i) {
+        e0[i] = x[3 * i];
+        e1[i] = x[3 * i + 1];
+        e2[i] = x[3 * i + 2];
+      }
+      Dft<M, DIR>::run(e0);
+      Dft<M, DIR>::run(e1);
+      Dft<M, DIR>::run(e2);
+      dft3_combine<N, DIR>(x, e0, e1, e2, std::make_integer_sequence<int, M>{});
+    } else {
+      float2 e[N / 2], o[N / 2];
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        e[i] = x[2 * i];
+        o[i] = x[2 * i + 1];
+      }
+      Dft<N / 2, DIR>::run(e);
+      Dft<N / 2, DIR>::run(o);
+      dft_combine<N, DIR>(x, e, o, std::make_integer_sequence<int, N / 2>{});
     }
-    Dft<N / 2, DIR>::run(e);
-    Dft<N / 2, DIR>::run(o);
-    dft_combine<N, DIR>(x, e, o, std::make_integer_sequence<int, N / 2>{});
   }
 };
 
@@ -121,11 +169,12 @@ template <> struct Split<128> { static constexpr int A = 16, B = 8; };
 template <> struct Split<256> { static constexpr int A = 16, B = 16; };
 template <> struct Split<512> { static constexpr int A = 32, B = 16; };
 template <> struct Split<1024> { static constexpr int A = 32, B = 32; };
+template <> struct Split<384> { static constexpr int A = 24, B = 16; };  // 3 * 2^7
 
-// Offset of the twiddle table of length L inside the concatenated table
-// (lengths 8, 16, ..., 1024 stored back to back): 8 + 16 + ... + L/2 = L - 8.
-__host__ __device__ constexpr int twiddle_offset(int L) { return L - 8; }
-constexpr int kTwiddleTotal = 2048 - 8;
+// Offset of the twiddle table of length L inside the concatenated table: lengths
+// 8, 16, ..., 1024 back to back (8 + 16 + ... + L/2 = L - 8), then 384.
+__host__ __device__ constexpr int twiddle_offset(int L) { return L == 384 ? 2040 : L - 8; }
+constexpr int kTwiddleTotal = 2040 + 384;
 
 }  // namespace dev
 }  // namespace sl

@@ -32,7 +32,7 @@ __device__ float2 g_twiddle[kTwiddleTotal];
 // several independent CTAs share an SM and overlap each other's memory latency.
 __host__ __device__ constexpr int col_tile_of(int L) {
   return L == 8 ? 32 : L == 16 ? 32 : L == 32 ? 16 : L == 64 ? 16 : L == 128 ? 8 : L == 256 ? 8
-       : L == 512 ? 4 : 4;
+       : 4;  // 384, 512, 1024
 }
 
 // Line geometry: TC lines per CTA, T = TC * A threads (one pass-1 item per thread;
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A) k_row(RowArgs p) {
     const int pr = pair0 + line;
     if (pr >= npairs) continue;
     const float2 z = sm[line * L + k];
-    const float2 w = sm[line * L + ((L - k) & (L - 1))];
+    const float2 w = sm[line * L + (k == 0 ? 0 : L - k)];
     out[tm.at(2 * pr, k)] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
     out[tm.at(2 * pr + 1, k)] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
   }
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A)
     for (int it = tid; it < PAIRS * HP; it += T) {
       const int line = it / HP, kk = it % HP;
       const float2 z = sm[line * L + kk];
-      const float2 w = sm[line * L + ((L - kk) & (L - 1))];
+      const float2 w = sm[line * L + (kk == 0 ? 0 : L - kk)];
       out[tm.at(r0 + 2 * line, kk)] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
       out[tm.at(r0 + 2 * line + 1, kk)] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
     }

@@ -99,9 +99,10 @@ static sl_status init_device(int dev) {
   if (dev < 0 || dev >= 64) return fail(SL_EINVAL, "device ordinal out of range");
   if (g_dev_init[dev]) return SL_OK;
   std::vector<float2> tw(sl::dev::kTwiddleTotal);
-  for (int L = 8; L <= 1024; L *= 2) {
+  for (int L : {8, 16, 32, 64, 128, 256, 512, 1024, 384}) {
     int A = 0, B = 0;
     switch (L) {
+      case 384: A = 24; B = 16; break;
       case 8: A = 4; B = 2; break;
       case 16: A = 4; B = 4; break;
       case 32: A = 8; B = 4; break;
@@ -155,6 +156,7 @@ static cudaError_t launch_col(int L, dim3 grid, cudaStream_t st, const ColArgs& 
     case 256: return launch_col_t<256, MODE>(grid, st, a);
     case 512: return launch_col_t<512, MODE>(grid, st, a);
     case 1024: return launch_col_t<1024, MODE>(grid, st, a);
+    case 384: return launch_col_t<384, MODE>(grid, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -235,6 +237,7 @@ static cudaError_t launch_row_pipe(int L, int slots, int L0, int NPp, cudaStream
     case 256: return launch_row_pipe_t<256, MODE>(slots, L0, NPp, st, a);
     case 512: return launch_row_pipe_t<512, MODE>(slots, L0, NPp, st, a);
     case 1024: return launch_row_pipe_t<1024, MODE>(slots, L0, NPp, st, a);
+    case 384: return launch_row_pipe_t<384, MODE>(slots, L0, NPp, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -260,6 +263,7 @@ static cudaError_t launch_col_inv_pipe(int L, int nitems, cudaStream_t st, const
     case 256: return launch_col_inv_pipe_t<256>(nitems, st, a);
     case 512: return launch_col_inv_pipe_t<512>(nitems, st, a);
     case 1024: return launch_col_inv_pipe_t<1024>(nitems, st, a);
+    case 384: return launch_col_inv_pipe_t<384>(nitems, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -274,6 +278,7 @@ static cudaError_t launch_col_fwd_pipe(int L, int nitems, cudaStream_t st, const
     case 256: return launch_col_fwd_pipe_t<256>(nitems, st, a);
     case 512: return launch_col_fwd_pipe_t<512>(nitems, st, a);
     case 1024: return launch_col_fwd_pipe_t<1024>(nitems, st, a);
+    case 384: return launch_col_fwd_pipe_t<384>(nitems, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -310,6 +315,7 @@ static cudaError_t launch_row(int L, int slots, int L0, cudaStream_t st, const R
     case 256: return launch_row_t<256, MODE>(slots, L0, st, a);
     case 512: return launch_row_t<512, MODE>(slots, L0, st, a);
     case 1024: return launch_row_t<1024, MODE>(slots, L0, st, a);
+    case 384: return launch_row_t<384, MODE>(slots, L0, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -557,8 +563,9 @@ sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const 
   spec.full = fullSystem != 0;
   for (int i = 0; i < ndim; ++i) {
     if (dims[i] < 8) return fail(SL_EINVAL, "every dimension must be >= 8");
-    if (!is_pow2(dims[i]) || dims[i] > 1024)
-      return fail(SL_ENOTSUP, "dimensions must be powers of two in [8, 1024]");
+    const bool ok = (is_pow2(dims[i]) && dims[i] <= 1024) || (ndim == 2 && dims[i] == 384);
+    if (!ok)
+      return fail(SL_ENOTSUP, "dimensions must be powers of two in [8, 1024] (2D: or 384)");
     spec.dims[i] = dims[i];
   }
   for (int j = 0; j < nScales; ++j) {
@@ -1018,6 +1025,22 @@ static sl_status backward(const Plan& P, const float* coeffs, float* x, bool use
   return inv_final(P, parts_used(P), use_invpsi, x, st);
 }
 
+// Fused denoise: per group, filter, C2R + threshold + R2C in shared memory, accumulate.
+static sl_status denoise_plan(const Plan& P, const float* noisy, float* out, float sigma,
+                              const float* K, cudaStream_t st) {
+  SL_TRY(spectrum_of(P, noisy, st));
+  for (int g = 0; g < P.ngroups; ++g) {
+    const int j0 = g * P.G;
+    const int nf = std::min(P.G, P.R - j0);
+    Thresholds t;
+    fill_thresholds(P.bank, j0, nf, sigma, K, &t);
+    SL_TRY(fwd_filter_pass(P, j0, nf, st));
+    SL_TRY(slab_pass<sl::dev::ROW_RT>(P, j0, nf, nullptr, nullptr, &t, st));
+    SL_TRY(inv_acc_pass(P, g, j0, nf, st));
+  }
+  return inv_final(P, parts_used(P), true, out, st);
+}
+
 // ------------------------------------------------- cluster-fused orchestration ---
 
 // x -> spectrum (one cluster) -> per filter C2R (all clusters).
@@ -1122,19 +1145,7 @@ sl_status sl_denoise(const sl_bank* b, const float* noisy, float* out, float sig
   SL_TRY(check_call(b));
   if (!noisy || !out || !K) return fail(SL_EINVAL, "noisy, out or K is NULL");
   if (!(sigma >= 0.f) || !std::isfinite(sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
-  cudaStream_t st = (cudaStream_t)stream;
-  const Plan P = plan_of(b);
-  SL_TRY(spectrum_of(P, noisy, st));
-  for (int g = 0; g < P.ngroups; ++g) {
-    const int j0 = g * P.G;
-    const int nf = std::min(P.G, P.R - j0);
-    Thresholds t;
-    fill_thresholds(b, j0, nf, sigma, K, &t);
-    SL_TRY(fwd_filter_pass(P, j0, nf, st));
-    SL_TRY(slab_pass<sl::dev::ROW_RT>(P, j0, nf, nullptr, nullptr, &t, st));
-    SL_TRY(inv_acc_pass(P, g, j0, nf, st));
-  }
-  return inv_final(P, parts_used(P), true, out, st);
+  return denoise_plan(plan_of(b), noisy, out, sigma, K, (cudaStream_t)stream);
 }
 
 sl_status sl_fwdinv_host(const sl_bank* cb, const float* x_host, float* y_host, void* stream) {
@@ -1225,6 +1236,480 @@ sl_status sl_profile_read(const char** names, int64_t* launches, double* ms, dou
   }
   if (count) *count = std::min(i, cap);
   return SL_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched runs ---
+// A batch holds n transforms: image i on bank banks[i], any mix of shapes. Images are
+// spread over K branches, longest estimated cost first onto the least loaded branch.
+// Each branch owns a workspace (spectrum, group slab, partials) and a stream and runs
+// its images one after another, so the single-image stages of one image (row and
+// pencil FFTs of the signal, the final reduction) overlap the filter stages of others.
+// The fork/join is captured into a CUDA graph once and then replayed by one
+// cudaGraphLaunch per call; it is captured again when the data pointers (or the
+// denoise thresholds) differ from the captured ones. Per distinct bank the batch also
+// keeps its own filters-per-group cap (the slab width), which the autotuner sets.
+
+namespace {
+
+enum BatchOp { BOP_FWD = 0, BOP_INV = 1, BOP_FWDINV = 2, BOP_DENOISE = 3, BOP_COUNT = 4 };
+
+struct BatchIO {
+  const float* const* x = nullptr;   // forward / fwdinv / denoise input
+  float* const* c = nullptr;         // coefficients (forward output, inverse input)
+  float* const* y = nullptr;         // inverse / fwdinv / denoise output
+  float sigma = 0.f;
+  const float* const* K = nullptr;   // denoise: per image, nScales of its bank
+};
+
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> key;
+};
+
+}  // namespace
+
+struct sl_batch {
+  int device = -1;
+  int n = 0;
+  std::vector<const sl_bank*> banks;
+  std::vector<const sl_bank*> distinct;  // distinct banks, in first-use order
+  std::vector<int> shape_of;             // image -> index into distinct
+  std::vector<int> gmax;                 // per distinct bank: filters-per-group cap
+  int K = 1;                             // branches
+  int use_graph = 1;
+  std::vector<std::vector<int>> order;   // branch -> its images, in issue order
+  std::vector<float2*> ws;               // branch workspaces
+  std::vector<int64_t> ws_elems;
+  std::vector<cudaStream_t> streams;     // [K]
+  std::vector<cudaEvent_t> ev;           // [K + 1]: fork, then one join per branch
+  cudaStream_t cap = nullptr;            // capture origin
+  BatchGraph graph[BOP_COUNT];
+};
+
+// Group layout of bank b with at most gmax filters per group (as plan_groups).
+static void group_plan(const sl_bank* b, int gmax, Plan& p) {
+  gmax = std::max(1, std::min(gmax, kMaxGroup));
+  p.ngroups = (b->R + gmax - 1) / gmax;
+  p.G = (b->R + p.ngroups - 1) / p.ngroups;
+  const int want = std::max(1, (4 * 148 + b->ntiles - 1) / b->ntiles);
+  p.fps = std::max(2, (p.G + want - 1) / want);
+  p.S = (p.G + p.fps - 1) / p.fps;
+}
+
+static int64_t plan_ws_elems(const Plan& p) {
+  return p.Nhp * (1 + (int64_t)p.G + (int64_t)p.ngroups * p.S);
+}
+
+static Plan batch_plan(const sl_batch* B, int i, float2* ws) {
+  const sl_bank* b = B->banks[i];
+  Plan p = plan_of(b);
+  group_plan(b, B->gmax[B->shape_of[i]], p);
+  p.xhat = ws;
+  p.scratch = ws + p.Nhp;
+  p.partial = ws + p.Nhp * (1 + (int64_t)p.G);
+  return p;
+}
+
+static double image_cost(const sl_bank* b) {
+  return (double)(b->R + 2) * (double)b->N * std::log2((double)b->N);
+}
+
+static void batch_release_graphs(sl_batch* B) {
+  for (BatchGraph& g : B->graph) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.key.clear();
+  }
+}
+
+static void batch_release_branches(sl_batch* B) {
+  batch_release_graphs(B);
+  for (float2* w : B->ws) cudaFree(w);
+  for (cudaStream_t s : B->streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : B->ev)
+    if (e) cudaEventDestroy(e);
+  B->ws.clear();
+  B->ws_elems.clear();
+  B->streams.clear();
+  B->ev.clear();
+  B->order.clear();
+}
+
+// Schedule the images over K branches and size each branch's workspace. Images of a
+// cluster-path bank share the bank's own buffers, so they form one job.
+static sl_status batch_schedule(sl_batch* B, int K) {
+  batch_release_branches(B);
+  struct Job { double cost; std::vector<int> imgs; };
+  std::vector<Job> jobs;
+  std::map<const sl_bank*, int> cl_job;
+  for (int i = 0; i < B->n; ++i) {
+    const sl_bank* b = B->banks[i];
+    if (b->cl) {
+      auto it = cl_job.find(b);
+      if (it == cl_job.end()) {
+        cl_job[b] = (int)jobs.size();
+        jobs.push_back(Job{0.0, {}});
+        it = cl_job.find(b);
+      }
+      jobs[it->second].cost += image_cost(b);
+      jobs[it->second].imgs.push_back(i);
+    } else {
+      jobs.push_back(Job{image_cost(b), {i}});
+    }
+  }
+  K = std::max(1, std::min<int>(K, (int)jobs.size()));
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [](const Job& a, const Job& b) { return a.cost > b.cost; });
+  std::vector<double> load(K, 0.0);
+  B->order.assign(K, {});
+  for (const Job& j : jobs) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += j.cost;
+    for (int i : j.imgs) B->order[k].push_back(i);
+  }
+  B->K = K;
+  B->ws.assign(K, nullptr);
+  B->ws_elems.assign(K, 0);
+  B->streams.assign(K, nullptr);
+  B->ev.assign(K + 1, nullptr);
+  for (int k = 0; k < K; ++k) {
+    int64_t need = 0;
+    for (int i : B->order[k])
+      if (!B->banks[i]->cl) need = std::max(need, plan_ws_elems(batch_plan(B, i, nullptr)));
+    B->ws_elems[k] = need;
+    if (need > 0 && cudaMalloc((void**)&B->ws[k], (size_t)need * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      B->ws[k] = nullptr;
+      batch_release_branches(B);
+      return fail(SL_ENOMEM, "allocating batch workspaces");
+    }
+    SL_CUDA(cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking));
+  }
+  for (int k = 0; k <= K; ++k) SL_CUDA(cudaEventCreateWithFlags(&B->ev[k], cudaEventDisableTiming));
+  return SL_OK;
+}
+
+static sl_status batch_image(const sl_batch* B, int i, int op, const BatchIO& io, int k,
+                             cudaStream_t st) {
+  const sl_bank* b = B->banks[i];
+  if (b->cl) {
+    if (op == BOP_FWD || op == BOP_FWDINV) SL_TRY(cl_forward(b, io.x[i], io.c[i], st));
+    if (op == BOP_INV || op == BOP_FWDINV) SL_TRY(cl_backward(b, io.c[i], io.y[i], true, st));
+    if (op == BOP_DENOISE) return fail(SL_ENOTSUP, "batched denoise needs general-path banks");
+    return SL_OK;
+  }
+  const Plan P = batch_plan(B, i, B->ws[k]);
+  if (op == BOP_FWD || op == BOP_FWDINV) SL_TRY(forward_plan(P, io.x[i], io.c[i], st));
+  if (op == BOP_INV || op == BOP_FWDINV) SL_TRY(backward(P, io.c[i], io.y[i], true, st));
+  if (op == BOP_DENOISE) SL_TRY(denoise_plan(P, io.x[i], io.y[i], io.sigma, io.K[i], st));
+  return SL_OK;
+}
+
+// Fork from `origin` into the branch streams, run every branch, join back.
+static sl_status batch_issue(const sl_batch* B, int op, const BatchIO& io, cudaStream_t origin) {
+  SL_CUDA(cudaEventRecord(B->ev[0], origin));
+  for (int k = 0; k < B->K; ++k) {
+    if (B->order[k].empty()) continue;
+    cudaStream_t st = B->streams[k];
+    SL_CUDA(cudaStreamWaitEvent(st, B->ev[0], 0));
+    for (int i : B->order[k]) SL_TRY(batch_image(B, i, op, io, k, st));
+    SL_CUDA(cudaEventRecord(B->ev[k + 1], st));
+    SL_CUDA(cudaStreamWaitEvent(origin, B->ev[k + 1], 0));
+  }
+  return SL_OK;
+}
+
+static std::vector<uint64_t> batch_key(const sl_batch* B, int op, const BatchIO& io) {
+  std::vector<uint64_t> key;
+  for (int i = 0; i < B->n; ++i) {
+    key.push_back(io.x ? (uint64_t)(uintptr_t)io.x[i] : 0);
+    key.push_back(io.c ? (uint64_t)(uintptr_t)io.c[i] : 0);
+    key.push_back(io.y ? (uint64_t)(uintptr_t)io.y[i] : 0);
+  }
+  if (op == BOP_DENOISE) {
+    uint32_t u;
+    std::memcpy(&u, &io.sigma, 4);
+    key.push_back(u);
+    for (int i = 0; i < B->n; ++i)
+      for (int j = 0; j < B->banks[i]->spec.J; ++j) {
+        std::memcpy(&u, &io.K[i][j], 4);
+        key.push_back(u);
+      }
+  }
+  return key;
+}
+
+static sl_status batch_check_io(const sl_batch* B, int op, const BatchIO& io) {
+  if (!B) return fail(SL_EINVAL, "batch is NULL");
+  int cur = -1;
+  SL_CUDA(cudaGetDevice(&cur));
+  if (cur != B->device) return fail(SL_EINVAL, "current CUDA device differs from the batch's");
+  const bool need_x = op != BOP_INV, need_c = op != BOP_DENOISE, need_y = op != BOP_FWD;
+  if ((need_x && !io.x) || (need_c && !io.c) || (need_y && !io.y))
+    return fail(SL_EINVAL, "a pointer array is NULL");
+  for (int i = 0; i < B->n; ++i)
+    if ((need_x && !io.x[i]) || (need_c && !io.c[i]) || (need_y && !io.y[i]))
+      return fail(SL_EINVAL, "image " + std::to_string(i) + ": NULL data pointer");
+  if (op == BOP_DENOISE) {
+    if (!io.K) return fail(SL_EINVAL, "K is NULL");
+    if (!(io.sigma >= 0.f) || !std::isfinite(io.sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
+    for (int i = 0; i < B->n; ++i) {
+      if (!io.K[i]) return fail(SL_EINVAL, "image " + std::to_string(i) + ": K is NULL");
+      for (int j = 0; j < B->banks[i]->spec.J; ++j)
+        if (!std::isfinite(io.K[i][j])) return fail(SL_EINVAL, "K must be finite");
+    }
+  }
+  return SL_OK;
+}
+
+static sl_status batch_run(sl_batch* B, int op, const BatchIO& io, cudaStream_t st) {
+  SL_TRY(batch_check_io(B, op, io));
+  if (!B->use_graph || g_prof_on) return batch_issue(B, op, io, st);
+  BatchGraph& G = B->graph[op];
+  std::vector<uint64_t> key = batch_key(B, op, io);
+  if (!G.exec || G.key != key) {
+    cudaGraph_t g = nullptr;
+    SL_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
+    const sl_status s = batch_issue(B, op, io, B->cap);
+    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+    if (s != SL_OK) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "capturing the batch");
+    if (G.exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(G.exec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+      }
+    }
+    if (!G.exec) e = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      G.exec = nullptr;
+      return cuda_fail(e, "instantiating the batch graph");
+    }
+    G.key = std::move(key);
+  }
+  SL_CUDA(cudaGraphLaunch(G.exec, st));
+  return SL_OK;
+}
+
+// Device time of `reps` calls of fn on st (minimum over calls), in ms.
+template <typename F>
+static sl_status time_min(cudaStream_t st, int reps, F&& fn, double* best) {
+  cudaEvent_t a, b;
+  SL_CUDA(cudaEventCreate(&a));
+  SL_CUDA(cudaEventCreate(&b));
+  *best = 1e300;
+  sl_status s = SL_OK;
+  for (int r = 0; r < reps && s == SL_OK; ++r) {
+    cudaEventRecord(a, st);
+    s = fn();
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (s == SL_OK && e != cudaSuccess) s = cuda_fail(e, "autotune timing");
+    float ms = 0.f;
+    if (s == SL_OK) cudaEventElapsedTime(&ms, a, b);
+    if (s == SL_OK && r > 0) *best = std::min(*best, (double)ms);  // first call warms up
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return s;
+}
+
+extern "C" {
+
+sl_status sl_batch_create(const sl_bank* const* banks, int n, const sl_batch_options* opt,
+                          sl_batch** out) {
+  if (!out) return fail(SL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!banks || n <= 0) return fail(SL_EINVAL, "banks is NULL or n <= 0");
+  std::unique_ptr<sl_batch> B(new sl_batch());
+  B->n = n;
+  for (int i = 0; i < n; ++i) {
+    SL_TRY(check_call(banks[i]));
+    B->banks.push_back(banks[i]);
+    auto it = std::find(B->distinct.begin(), B->distinct.end(), banks[i]);
+    if (it == B->distinct.end()) {
+      B->shape_of.push_back((int)B->distinct.size());
+      B->distinct.push_back(banks[i]);
+      B->gmax.push_back(banks[i]->G);
+    } else {
+      B->shape_of.push_back((int)(it - B->distinct.begin()));
+    }
+  }
+  B->device = banks[0]->device;
+  int K = 0;
+  if (opt) {
+    if (opt->branches < 0) return fail(SL_EINVAL, "branches must be >= 0");
+    K = opt->branches;
+    B->use_graph = opt->no_graph ? 0 : 1;
+  }
+  if (K == 0) K = 4;
+  SL_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  sl_status s = batch_schedule(B.get(), K);
+  if (s != SL_OK) {
+    cudaStreamDestroy(B->cap);
+    return s;
+  }
+  *out = B.release();
+  return SL_OK;
+}
+
+void sl_batch_free(sl_batch* B) {
+  if (!B) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (B->device >= 0) cudaSetDevice(B->device);
+  batch_release_branches(B);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete B;
+}
+
+sl_status sl_batch_info(const sl_batch* B, int* branches, int* branch_of, int* group_cap) {
+  if (!B) return fail(SL_EINVAL, "batch is NULL");
+  if (branches) *branches = B->K;
+  for (int k = 0; k < B->K; ++k)
+    for (int i : B->order[k]) {
+      if (branch_of) branch_of[i] = k;
+      if (group_cap) group_cap[i] = B->banks[i]->cl ? B->banks[i]->R : B->gmax[B->shape_of[i]];
+    }
+  return SL_OK;
+}
+
+sl_status sl_batch_forward(sl_batch* B, const float* const* x, float* const* coeffs, void* stream) {
+  BatchIO io;
+  io.x = x;
+  io.c = coeffs;
+  return batch_run(B, BOP_FWD, io, (cudaStream_t)stream);
+}
+
+sl_status sl_batch_inverse(sl_batch* B, const float* const* coeffs, float* const* x, void* stream) {
+  BatchIO io;
+  io.c = const_cast<float* const*>(coeffs);
+  io.y = x;
+  return batch_run(B, BOP_INV, io, (cudaStream_t)stream);
+}
+
+sl_status sl_batch_fwdinv(sl_batch* B, const float* const* x, float* const* coeffs, float* const* y,
+                          void* stream) {
+  BatchIO io;
+  io.x = x;
+  io.c = coeffs;
+  io.y = y;
+  return batch_run(B, BOP_FWDINV, io, (cudaStream_t)stream);
+}
+
+sl_status sl_batch_denoise(sl_batch* B, const float* const* noisy, float* const* out, float sigma,
+                           const float* const* K, void* stream) {
+  BatchIO io;
+  io.x = noisy;
+  io.y = out;
+  io.sigma = sigma;
+  io.K = K;
+  return batch_run(B, BOP_DENOISE, io, (cudaStream_t)stream);
+}
+
+sl_status sl_batch_autotune(sl_batch* B, const float* const* x, float* const* coeffs,
+                            float* const* y, int reps, void* stream, double* best_ms) {
+  BatchIO io;
+  io.x = x;
+  io.c = coeffs;
+  io.y = y;
+  SL_TRY(batch_check_io(B, BOP_FWDINV, io));
+  if (reps < 2) return fail(SL_EINVAL, "reps must be >= 2");
+  cudaStream_t st = (cudaStream_t)stream;
+  SL_CUDA(cudaStreamSynchronize(st));
+  // 1. per distinct bank, the filters-per-group cap: one image of that shape, alone
+  for (size_t d = 0; d < B->distinct.size(); ++d) {
+    const sl_bank* b = B->distinct[d];
+    if (b->cl) continue;
+    int img = 0;
+    while (B->shape_of[img] != (int)d) ++img;
+    std::vector<int> cand = {b->G, b->R, (b->R + 1) / 2, (b->R + 3) / 4, (b->R + 7) / 8};
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    double best = 1e300;
+    int best_g = B->gmax[d];
+    for (int g : cand) {
+      if (g < 2 || g > kMaxGroup) continue;
+      Plan p = plan_of(b);
+      group_plan(b, g, p);
+      const int64_t need = plan_ws_elems(p);
+      if ((double)need * sizeof(float2) > 1024.0 * 1024.0 * 1024.0) continue;  // 1 GiB cap
+      float2* ws = nullptr;
+      if (cudaMalloc((void**)&ws, (size_t)need * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      p.xhat = ws;
+      p.scratch = ws + p.Nhp;
+      p.partial = ws + p.Nhp * (1 + (int64_t)p.G);
+      double ms = 0.0;
+      sl_status s = time_min(st, reps, [&]() -> sl_status {
+        SL_TRY(forward_plan(p, x[img], coeffs[img], st));
+        return backward(p, coeffs[img], y[img], true, st);
+      }, &ms);
+      cudaFree(ws);
+      SL_TRY(s);
+      if (ms < best) {
+        best = ms;
+        best_g = g;
+      }
+    }
+    B->gmax[d] = best_g;
+  }
+  // 2. branch count: the whole batch, captured as it will run
+  double best = 1e300;
+  int best_k = B->K;
+  for (int k : {1, 2, 3, 4, 6, 8, 12, 16}) {
+    if (k > B->n) break;
+    SL_TRY(batch_schedule(B, k));
+    double ms = 0.0;
+    SL_TRY(time_min(st, reps, [&]() { return batch_run(B, BOP_FWDINV, io, st); }, &ms));
+    if (ms < best * 0.99) {  // prefer fewer branches unless clearly faster
+      best = ms;
+      best_k = k;
+    }
+  }
+  SL_TRY(batch_schedule(B, best_k));
+  if (best_ms) *best_ms = best;
+  return SL_OK;
+}
+
+// One-shot forms: build a batch (no graph), run it, wait for it, free it.
+sl_status sl_forward_batch(const sl_bank* const* banks, int n, const float* const* x,
+                           float* const* coeffs, void* stream) {
+  sl_batch_options o{};
+  o.no_graph = 1;
+  sl_batch* B = nullptr;
+  SL_TRY(sl_batch_create(banks, n, &o, &B));
+  sl_status s = sl_batch_forward(B, x, coeffs, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  sl_batch_free(B);
+  if (s == SL_OK && e != cudaSuccess) s = cuda_fail(e, "sl_forward_batch");
+  return s;
+}
+
+sl_status sl_inverse_batch(const sl_bank* const* banks, int n, const float* const* coeffs,
+                           float* const* x, void* stream) {
+  sl_batch_options o{};
+  o.no_graph = 1;
+  sl_batch* B = nullptr;
+  SL_TRY(sl_batch_create(banks, n, &o, &B));
+  sl_status s = sl_batch_inverse(B, coeffs, x, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  sl_batch_free(B);
+  if (s == SL_OK && e != cudaSuccess) s = cuda_fail(e, "sl_inverse_batch");
+  return s;
 }
 
 }  // extern "C"

@@ -51,6 +51,16 @@ SIGNATURES = {
     "sl_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _c_float_p, _vp]),
     "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sl_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sl_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "sl_batch_free": (None, [_vp]),
+    "sl_batch_info": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
+    "sl_batch_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_batch_inverse": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_batch_fwdinv": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sl_batch_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp, _vp]),
+    "sl_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, _c_double_p]),
+    "sl_forward_batch": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "sl_inverse_batch": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "sl_mlp_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
     "sl_mlp_free": (None, [_vp]),
     "sl_mlp_num_params": (ctypes.c_int, [_vp]),
@@ -430,3 +440,109 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ batches ---
+
+class _BatchOptions(ctypes.Structure):
+    _fields_ = [("branches", ctypes.c_int), ("no_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+def _ptr_array(tensors, what, sizes):
+    arr = (_vp * len(tensors))()
+    for i, (t, n) in enumerate(zip(tensors, sizes)):
+        arr[i] = _dev_ptr(t, f"{what}[{i}]", n)
+    return arr
+
+
+class Batch:
+    """Many images of (possibly) different shapes transformed together (sl_batch_*):
+    image i uses banks[i]. Inputs and outputs are lists of device tensors; the
+    pointer arrays are built here, the work runs in the library."""
+
+    def __init__(self, banks: Sequence["Bank"], branches: int = 0, graph: bool = True):
+        self.banks = list(banks)
+        n = len(self.banks)
+        self._handles = (_vp * n)(*[b.handle for b in self.banks])
+        opt = _BatchOptions(int(branches), 0 if graph else 1)
+        h = _vp()
+        _check(lib().sl_batch_create(self._handles, n, ctypes.byref(opt), ctypes.byref(h)),
+               "sl_batch_create")
+        self.handle = h.value
+
+    def _sizes(self, coeffs=False):
+        return [b.R * b.N if coeffs else b.N for b in self.banks]
+
+    def info(self):
+        n = len(self.banks)
+        K = ctypes.c_int()
+        br = (ctypes.c_int * n)()
+        gc = (ctypes.c_int * n)()
+        _check(lib().sl_batch_info(self.handle, ctypes.byref(K), br, gc), "sl_batch_info")
+        return {"branches": K.value, "branch_of": list(br), "group_cap": list(gc)}
+
+    def forward(self, xs, cs, stream=None):
+        _check(lib().sl_batch_forward(self.handle, _ptr_array(xs, "x", self._sizes()),
+                                      _ptr_array(cs, "coeffs", self._sizes(True)),
+                                      _stream_ptr(stream)), "sl_batch_forward")
+        return cs
+
+    def inverse(self, cs, ys, stream=None):
+        _check(lib().sl_batch_inverse(self.handle, _ptr_array(cs, "coeffs", self._sizes(True)),
+                                      _ptr_array(ys, "x", self._sizes()),
+                                      _stream_ptr(stream)), "sl_batch_inverse")
+        return ys
+
+    def fwdinv(self, xs, cs, ys, stream=None):
+        _check(lib().sl_batch_fwdinv(self.handle, _ptr_array(xs, "x", self._sizes()),
+                                     _ptr_array(cs, "coeffs", self._sizes(True)),
+                                     _ptr_array(ys, "y", self._sizes()),
+                                     _stream_ptr(stream)), "sl_batch_fwdinv")
+        return ys
+
+    def denoise(self, xs, ys, sigma: float, K, stream=None):
+        """K: one list of nScales values per image (or one list for all)."""
+        Ks = K if (len(K) and isinstance(K[0], (list, tuple, np.ndarray))) else [K] * len(xs)
+        self._Kbufs = [(ctypes.c_float * len(k))(*[float(v) for v in k]) for k in Ks]
+        for b, k in zip(self.banks, Ks):
+            b._check_K(k)
+        kp = (_vp * len(Ks))(*[ctypes.cast(k, _vp).value for k in self._Kbufs])
+        _check(lib().sl_batch_denoise(self.handle, _ptr_array(xs, "noisy", self._sizes()),
+                                      _ptr_array(ys, "out", self._sizes()), float(sigma), kp,
+                                      _stream_ptr(stream)), "sl_batch_denoise")
+        return ys
+
+    def autotune(self, xs, cs, ys, reps: int = 3, stream=None) -> float:
+        best = ctypes.c_double()
+        _check(lib().sl_batch_autotune(self.handle, _ptr_array(xs, "x", self._sizes()),
+                                       _ptr_array(cs, "coeffs", self._sizes(True)),
+                                       _ptr_array(ys, "y", self._sizes()), int(reps),
+                                       _stream_ptr(stream), ctypes.byref(best)),
+               "sl_batch_autotune")
+        return best.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sl_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sl_forward_batch(banks: Sequence["Bank"], xs, cs, stream=None) -> None:
+    h = (_vp * len(banks))(*[b.handle for b in banks])
+    _check(lib().sl_forward_batch(h, len(banks), _ptr_array(xs, "x", [b.N for b in banks]),
+                                  _ptr_array(cs, "coeffs", [b.R * b.N for b in banks]),
+                                  _stream_ptr(stream)), "sl_forward_batch")
+
+
+def sl_inverse_batch(banks: Sequence["Bank"], cs, ys, stream=None) -> None:
+    h = (_vp * len(banks))(*[b.handle for b in banks])
+    _check(lib().sl_inverse_batch(h, len(banks), _ptr_array(cs, "coeffs", [b.R * b.N for b in banks]),
+                                  _ptr_array(ys, "x", [b.N for b in banks]),
+                                  _stream_ptr(stream)), "sl_inverse_batch")

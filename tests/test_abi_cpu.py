@@ -52,6 +52,8 @@ def test_status_strings(L):
     ((16, 16), 0, (), "SL_EINVAL"),            # no scales
     ((16, 16), 1, (-1,), "SL_EINVAL"),         # negative level
     ((16, 16, 256), 1, (0,), "SL_ENOTSUP"),    # 3D plane larger than one CTA holds
+    ((768, 64), 1, (1,), "SL_ENOTSUP"),        # 3 * 2^8: only 384 has a mixed-radix plan
+    ((384, 16, 16), 1, (0,), "SL_ENOTSUP"),    # 384 is a 2D size only
 ])
 def test_invalid_arguments_are_rejected(L, dims, J, sl, err):
     with pytest.raises(S.ShearletError) as ei:
@@ -70,7 +72,8 @@ def test_transform_on_host_only_bank_is_an_error(L):
 CASES = [((64, 64), 3, (0, 1, 1), False), ((64, 32), 2, (1, 1), False),
          ((256, 256), 2, (1, 1), False), ((32, 32), 2, (1, 2), True),
          ((16, 16, 16), 2, (0, 1), False), ((32, 16, 8), 2, (1, 1), False),
-         ((16, 16, 16), 1, (1,), True)]
+         ((16, 16, 16), 1, (1,), True), ((384, 64), 2, (1, 1), False),
+         ((64, 384), 3, (0, 1, 1), False)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=str)
@@ -101,5 +104,16 @@ def test_library_bank_matches_oracle_at_512():
     s = oracle_system((512, 512), 4, (1, 1, 2, 2))
     for j in range(0, b.R, 6):
         assert np.max(np.abs(b.eval_f64(j) - s.psi_hat(j)[:, :257])) <= 1e-12
+    assert abs(b.A - s.A) <= 1e-12
+    b.close()
+
+
+def test_library_bank_matches_oracle_at_384():
+    """A 384^2 grid (3 * 2^7, one of the batch sizes) with the 49-filter system."""
+    b = S.Bank((384, 384), 4, (1, 1, 2, 2), device=-1)
+    s = oracle_system((384, 384), 4, (1, 1, 2, 2))
+    assert b.R == 49
+    for j in list(range(0, b.R, 8)) + [b.R - 1]:
+        assert np.max(np.abs(b.eval_f64(j) - s.psi_hat(j)[:, :193])) <= 1e-12
     assert abs(b.A - s.A) <= 1e-12
     b.close()
