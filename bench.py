@@ -382,6 +382,10 @@ def extras(b, x, clean, C, flush, args):
         "note": "BF16 mma.sync tensor cores, FP32 accumulate; flops count the two "
                 "dense layers and the output dot (backward ~2x forward)"}
     try:
+        out["tc_bf16_vs_fp32"] = tc_vs_fp32(b, x, flush, steps, peak)
+    except Exception as e:  # report, do not fail the headline line
+        out["tc_bf16_vs_fp32"] = {"error": str(e)}
+    try:
         out["batched_uneven_64"] = batched_uneven(flush, steps, peak)
     except Exception as e:  # report, do not fail the headline line
         out["batched_uneven_64"] = {"error": str(e)}
@@ -404,6 +408,37 @@ def extras(b, x, clean, C, flush, args):
     except Exception as e:  # report, do not fail the headline line
         out["3d_128_fwd_inv"] = {"error": str(e)}
     return out
+
+
+def tc_vs_fp32(b, x, flush, steps: int, peak: float) -> dict:
+    """The same 512^2 forward + inverse with the pencil passes on the tensor cores
+    (split BF16, FP32 accumulate) and in FP32, each with its error against an FP64
+    evaluation (numpy FFTs in double precision with the bank's FP64 filters, for a
+    sample of subbands) and its reconstruction error."""
+    import numpy as np
+    import torch
+    from paper_1402_5670_b300.shearlet import Bank
+    bt = Bank(DIMS, J, LEVELS, device=b.device, precision="tc_bf16")
+    xd = x.cpu().numpy().astype(np.float64)
+    X = np.fft.rfft2(xd)
+    js = (0, 7, 24, 48)
+    ref = {j: np.fft.irfft2(X * b.eval_f64(j), s=DIMS) for j in js}
+    res = {}
+    for name, bk in (("fp32", b), ("tc_bf16", bt)):
+        C = torch.empty((bk.R,) + DIMS, device="cuda")
+        y = torch.empty_like(x)
+        ms = _time_graph(lambda: (bk.forward(x, out=C), bk.inverse(C, out=y)), flush, steps)
+        err = max(float(np.max(np.abs(C[j].cpu().numpy() - ref[j])) / np.max(np.abs(ref[j])))
+                  for j in js)
+        alg = 8 * bk.N + 8 * bk.R * bk.N + 8 * bk.R * bk.Nh + 8 * bk.Nh
+        res[name] = {"ms": ms, "coeffs_per_s": bk.R * bk.N / (ms * 1e-3),
+                     "frac_hbm": alg / (ms * 1e-3) / 1e9 / peak,
+                     "max_rel_err_fwd_vs_fp64": err,
+                     "rel_err_reconstruction": float((y - x).abs().max() / x.abs().max())}
+        del C
+    res["error_sample"] = f"subbands {list(js)}, max-abs error / max-abs FP64 value"
+    bt.close()
+    return res
 
 
 def batched_uneven(flush, steps: int, peak: float) -> dict:

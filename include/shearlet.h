@@ -95,8 +95,19 @@ typedef struct {
    *                    shared memory (SL_ENOTSUP elsewhere).
    * Both paths compute the same result. */
   int path;
-  int reserved[7];
+  /* Arithmetic of the pencil passes (axis 0) inside the per-filter loops of
+   * sl_forward, sl_adjoint, sl_inverse and sl_denoise:
+   *   SL_PREC_FP32     FP32 register FFTs (error vs FP64 about 1e-6 relative);
+   *   SL_PREC_TC_BF16  radix-8 DFT stages as BF16 tensor-core matrix products with
+   *                    split operands (hi + lo) and FP32 accumulation; error vs FP64
+   *                    about 1e-5 relative. Needs the general path and n0 a power
+   *                    of two in [64, 1024] (SL_ENOTSUP otherwise).
+   * The last-axis passes, the single-signal FFTs and the FP64 division by Psi are
+   * the same in both modes. */
+  int precision;
+  int reserved[6];
 } sl_options;
+enum { SL_PREC_FP32 = 0, SL_PREC_TC_BF16 = 1 };
 
 /* sl_build_filters with options (opt may be NULL: defaults). */
 sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales,
@@ -125,6 +136,9 @@ sl_status sl_bank_norms(const sl_bank* bank, double* norms, double* A, double* B
 /* The kernel path the bank's transforms take: SL_PATH_GENERAL or SL_PATH_CLUSTER
  * (sl_denoise and sl_forward_noalloc always take the general path). */
 sl_status sl_bank_path(const sl_bank* bank, int* path);
+
+/* The bank's precision mode (SL_PREC_FP32 or SL_PREC_TC_BF16). */
+sl_status sl_bank_precision(const sl_bank* bank, int* precision);
 
 /* Number of half-spectrum points Nh = N / n_last * (n_last/2 + 1), and N. */
 sl_status sl_bank_sizes(const sl_bank* bank, int64_t* N, int64_t* Nh);

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libshearlet.so")
 SOURCES = ["shearlet.cu", "bank_host.cpp", "mlp.cu"]
-HEADERS = ["fft_core.cuh", "kernels2d.cuh", "kernels3d.cuh", "kernels_cluster.cuh", "bank_host.h"]
+HEADERS = ["fft_core.cuh", "kernels2d.cuh", "kernels3d.cuh", "kernels_cluster.cuh", "kernels_tc.cuh",
+           "bank_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

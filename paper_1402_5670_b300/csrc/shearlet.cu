@@ -20,6 +20,7 @@
 #include "bank_host.h"
 #include "kernels3d.cuh"
 #include "kernels_cluster.cuh"
+#include "kernels_tc.cuh"
 
 using sl::dev::ColArgs;
 using sl::dev::RowArgs;
@@ -120,6 +121,14 @@ static sl_status init_device(int dev) {
       }
   }
   SL_CUDA(cudaMemcpyToSymbol(sl::dev::g_twiddle, tw.data(), tw.size() * sizeof(float2)));
+  // full tables exp(-2 pi i m / L), m < L, for the tensor-core stages (powers of two)
+  std::vector<float2> wf(sl::dev::kTwiddleTotal, make_float2(0.f, 0.f));
+  for (int L = 8; L <= 1024; L *= 2)
+    for (int m = 0; m < L; ++m) {
+      const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)m / L;
+      wf[sl::dev::twiddle_offset(L) + m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  SL_CUDA(cudaMemcpyToSymbol(sl::dev::g_wfull, wf.data(), wf.size() * sizeof(float2)));
   g_dev_init[dev] = true;
   return SL_OK;
 }
@@ -279,6 +288,36 @@ static cudaError_t launch_col_fwd_pipe(int L, int nitems, cudaStream_t st, const
     case 512: return launch_col_fwd_pipe_t<512>(nitems, st, a);
     case 1024: return launch_col_fwd_pipe_t<1024>(nitems, st, a);
     case 384: return launch_col_fwd_pipe_t<384>(nitems, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Tensor-core (split BF16) pencil passes, persistent like the FP32 pipelines.
+template <int L>
+static cudaError_t launch_col_tc_t(bool fwd, int nitems, cudaStream_t st, const ColArgs& a) {
+  constexpr int smem = sl::dev::tc_col_smem_bytes<L>();
+  constexpr int T = sl::dev::kTcThreads;
+  if (fwd) {
+    auto k = sl::dev::k_col_fwd_tc<L>;
+    cudaError_t e = ensure_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nitems, persistent_grid(k, T, smem, 3000 + L));
+    return timed_launch("col_fwd_filter_tc", st, [&]() { k<<<grid, T, smem, st>>>(a); });
+  }
+  auto k = sl::dev::k_col_inv_tc<L>;
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(nitems, persistent_grid(k, T, smem, 4000 + L));
+  return timed_launch("col_inv_accumulate_tc", st, [&]() { k<<<grid, T, smem, st>>>(a); });
+}
+
+static cudaError_t launch_col_tc(int L, bool fwd, int nitems, cudaStream_t st, const ColArgs& a) {
+  switch (L) {
+    case 64: return launch_col_tc_t<64>(fwd, nitems, st, a);
+    case 128: return launch_col_tc_t<128>(fwd, nitems, st, a);
+    case 256: return launch_col_tc_t<256>(fwd, nitems, st, a);
+    case 512: return launch_col_tc_t<512>(fwd, nitems, st, a);
+    case 1024: return launch_col_tc_t<1024>(fwd, nitems, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -447,6 +486,7 @@ struct sl_bank {
   int ngroups = 1;
   int S = 1;        // partials per group
   int fps = 1;      // filters per partial
+  int prec = 0;     // SL_PREC_FP32 or SL_PREC_TC_BF16 (pencil passes on tensor cores)
   float* psi = nullptr;       // [R][Nhp] tile-major
   double* invPsi = nullptr;   // [Nhp] tile-major
   float2* xhat = nullptr;     // [Nhp] spectrum of the signal
@@ -554,6 +594,8 @@ sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const 
   *out = nullptr;
   const int path = opt ? opt->path : SL_PATH_AUTO;
   if (path < SL_PATH_AUTO || path > SL_PATH_CLUSTER) return fail(SL_EINVAL, "unknown path");
+  const int prec = opt ? opt->precision : SL_PREC_FP32;
+  if (prec != SL_PREC_FP32 && prec != SL_PREC_TC_BF16) return fail(SL_EINVAL, "unknown precision");
   if (ndim != 2 && ndim != 3) return fail(SL_EINVAL, "ndim must be 2 or 3");
   if (!dims || !shearLevels) return fail(SL_EINVAL, "dims or shearLevels is NULL");
   if (nScales < 1 || nScales > 8) return fail(SL_EINVAL, "nScales must be in [1, 8]");
@@ -577,9 +619,16 @@ sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const 
     if (dims[1] > 128 || dims[2] > 128)
       return fail(SL_ENOTSUP, "3D: axes 1 and 2 must be at most 128 (one plane per CTA)");
   }
+  if (prec == SL_PREC_TC_BF16) {
+    if (path == SL_PATH_CLUSTER)
+      return fail(SL_ENOTSUP, "tensor-core precision runs on the general path only");
+    if (!is_pow2(dims[0]) || dims[0] < 64)
+      return fail(SL_ENOTSUP, "tensor-core pencil passes need n0 a power of two in [64, 1024]");
+  }
   const int64_t N = spec.N(), Nh = spec.Nh();
   if (N > ((int64_t)1 << 31)) return fail(SL_ENOTSUP, "grid too large");
   std::unique_ptr<sl_bank> b(new sl_bank());
+  b->prec = prec;
   b->spec = spec;
   b->device = device;
   b->N = N;
@@ -744,6 +793,12 @@ sl_status sl_bank_path(const sl_bank* b, int* path) {
   return SL_OK;
 }
 
+sl_status sl_bank_precision(const sl_bank* b, int* precision) {
+  if (!b || !precision) return fail(SL_EINVAL, "NULL argument");
+  *precision = b->prec;
+  return SL_OK;
+}
+
 sl_status sl_bank_sizes(const sl_bank* b, int64_t* N, int64_t* Nh) {
   if (!b) return fail(SL_EINVAL, "bank is NULL");
   if (N) *N = b->N;
@@ -820,6 +875,7 @@ struct Plan {
   int G, ngroups, S, fps;
   const float* psi;   // tile-major [R][Nhp], or natural [R][Nh] when psi_natural
   int psi_natural;
+  int prec;           // 1: pencil passes of the filter loops on the tensor cores
   const double* invPsi;
   float2* xhat;       // [Nhp]
   float2* scratch;    // [G][Nhp]
@@ -844,6 +900,7 @@ static Plan plan_of(const sl_bank* b) {
   p.fps = b->fps;
   p.psi = b->psi;
   p.psi_natural = 0;
+  p.prec = b->prec;
   p.invPsi = b->invPsi;
   p.xhat = b->xhat;
   p.scratch = b->scratch;
@@ -933,6 +990,9 @@ static sl_status fwd_filter_pass(const Plan& P, int j0, int nf, cudaStream_t st)
   ca.j0 = j0;
   ca.nfilt = nf;
   g_next_bytes = 4.0 * (double)P.Nh * nf;  // filters read
+  if (P.prec && !P.psi_natural)
+    return launched(launch_col_tc((int)P.spec->dims[0], true, P.ntiles * nf, st, ca),
+                    "col_fwd_filter_tc");
   if (!P.psi_natural)
     return launched(launch_col_fwd_pipe((int)P.spec->dims[0], P.ntiles * nf, st, ca),
                     "col_fwd_filter");
@@ -954,6 +1014,9 @@ static sl_status inv_acc_pass(const Plan& P, int g_idx, int j0, int nf, cudaStre
   ca.part0 = g_idx * P.S;
   const int splits = (nf + P.fps - 1) / P.fps;
   g_next_bytes = 4.0 * (double)P.Nh * nf;  // filters read
+  if (P.prec)
+    return launched(launch_col_tc((int)P.spec->dims[0], false, P.ntiles * splits, st, ca),
+                    "col_inv_accumulate_tc");
   return launched(launch_col_inv_pipe((int)P.spec->dims[0], P.ntiles * splits, st, ca),
                   "col_inv_accumulate");
 }
@@ -1386,6 +1449,8 @@ static sl_status batch_schedule(sl_batch* B, int K) {
       batch_release_branches(B);
       return fail(SL_ENOMEM, "allocating batch workspaces");
     }
+    // pad pencils hold zeros, as in a bank's own scratch
+    if (need > 0) SL_CUDA(cudaMemset(B->ws[k], 0, (size_t)need * sizeof(float2)));
     SL_CUDA(cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking));
   }
   for (int k = 0; k <= K; ++k) SL_CUDA(cudaEventCreateWithFlags(&B->ev[k], cudaEventDisableTiming));

@@ -42,6 +42,7 @@ SIGNATURES = {
     "sl_bank_norms": (ctypes.c_int, [_vp, _c_double_p, _c_double_p, _c_double_p]),
     "sl_bank_sizes": (ctypes.c_int, [_vp, _c_int64_p, _c_int64_p]),
     "sl_bank_path": (ctypes.c_int, [_vp, _c_int_p]),
+    "sl_bank_precision": (ctypes.c_int, [_vp, _c_int_p]),
     "sl_bank_eval_f64": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p]),
     "sl_bank_filters_f32": (ctypes.c_int, [_vp, _c_float_p]),
     "sl_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -133,7 +134,11 @@ PATHS = {"auto": 0, "general": 1, "cluster": 2}
 
 
 class sl_options(ctypes.Structure):
-    _fields_ = [("path", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+PRECISIONS = {"fp32": 0, "tc_bf16": 1}
 
 
 def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
@@ -148,12 +153,14 @@ def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[
 
 
 def sl_build_filters_ex(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
-                        full_system: bool = False, device: int = 0, path: str = "auto") -> int:
+                        full_system: bool = False, device: int = 0, path: str = "auto",
+                        precision: str = "fp32") -> int:
     nd = len(dims)
     d = (ctypes.c_int64 * nd)(*[int(v) for v in dims])
     sl = (ctypes.c_int * len(shear_levels))(*[int(v) for v in shear_levels])
     opt = sl_options()
     opt.path = PATHS[path]
+    opt.precision = PRECISIONS[precision]
     out = _vp()
     _check(lib().sl_build_filters_ex(nd, d, int(n_scales), sl, int(bool(full_system)), int(device),
                                      ctypes.byref(opt), ctypes.byref(out)), "sl_build_filters_ex")
@@ -243,12 +250,14 @@ class Bank:
     """
 
     def __init__(self, dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
-                 full_system: bool = False, device: int = 0, path: str = "auto"):
+                 full_system: bool = False, device: int = 0, path: str = "auto",
+                 precision: str = "fp32"):
         if device >= 0:
             import torch
             torch.cuda.set_device(device)
         self.path = path
-        self.handle = sl_build_filters_ex(dims, n_scales, shear_levels, full_system, device, path)
+        self.handle = sl_build_filters_ex(dims, n_scales, shear_levels, full_system, device, path,
+                                          precision)
         L = lib()
         nd, R, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         dd = (ctypes.c_int64 * 3)()
@@ -270,6 +279,9 @@ class Bank:
         pth = ctypes.c_int()
         _check(L.sl_bank_path(self.handle, ctypes.byref(pth)), "sl_bank_path")
         self.kernel_path = {1: "general", 2: "cluster"}[pth.value]
+        pr = ctypes.c_int()
+        _check(L.sl_bank_precision(self.handle, ctypes.byref(pr)), "sl_bank_precision")
+        self.precision = {v: k for k, v in PRECISIONS.items()}[pr.value]
         self.scale_of = np.zeros(self.R, dtype=np.int32)
         self.cone_of = np.zeros(self.R, dtype=np.int32)
         self.k_of = np.zeros((self.R, 2), dtype=np.int32)
