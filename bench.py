@@ -151,6 +151,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------ our arm ---
 
+def max_over_ranks(ms: float, ws: int, device: str) -> float:
+    """The slowest rank's time: every rank contributes its own, all get the maximum
+    (NCCL on the GPUs; gloo with device="cpu")."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(coeffs_per_rank: int, n_gpus: int, ms: float) -> float:
+    """Coefficients of all ranks (one image each, weak scaling) per second."""
+    return coeffs_per_rank * n_gpus / (ms * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -209,11 +225,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = [a.elapsed_time(bb) for a, bb in ev]
     ms_step = sum(ms) / len(ms)
-    t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item())
-    value = R * N * n_gpus / (ms_step * 1e-3)
+    ms_step = max_over_ranks(ms_step, ws, "cuda")
+    value = whole_job_value(R * N, n_gpus, ms_step)
 
     # accuracy of this run's output: reconstruction error against the input
     rec_err = float((y - x).abs().max() / x.abs().max())
@@ -233,10 +246,7 @@ def run_ours(args):
         ev2[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(bb) for a, bb in ev2) / args.steps
-    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, ws, "cuda")
 
     # per-kernel device time (events around every launch), same steps and flushes;
     # a GPU-side sleep before each step lets the host queue the whole step first, so
