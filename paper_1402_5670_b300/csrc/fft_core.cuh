@@ -50,8 +50,8 @@ constexpr double cx_cos(double x) {
   return s;
 }
 
-// W_N^K = exp(-2 pi i K / N) for 0 <= K < 2N/3 (angle in (-4pi/3, 0]; the series
-// error there is still below 1e-23).
+// W_N^K = exp(-2 pi i K / N) for 0 <= K < 3N/4 (angle in (-3pi/2, 0]; the series
+// error there is still below 1e-21).
 template <int N, int K>
 struct Tw {
   static constexpr float re = (float)cx_cos(-2.0 * kPiD * K / N);
@@ -60,7 +60,8 @@ struct Tw {
 
 // ------------------------------------------------------------ register DFTs ---
 // In place, natural order in and out. DIR = -1: forward (e^{-i}), +1: inverse
-// (unnormalised). Radix-2 decimation in time, fully unrolled at compile time.
+// (unnormalised). Decimation in time (radix 4 where N is a multiple of 4 and at
+// least 16, else radix 3 or 2), fully unrolled at compile time.
 
 template <int N, int DIR>
 struct Dft;
@@ -122,10 +123,74 @@ __device__ __forceinline__ void dft3_combine(float2 (&x)[N], const float2 (&e0)[
   (dft3_bfly<N, DIR, K>(x, e0, e1, e2), ...);
 }
 
+// Radix-4 decimation in time for N divisible by 4 (N >= 16): with E_r the length-N/4
+// DFT of x[4n + r] and t_r = W_N^{r k} E_r[k],
+//   X[k] = (t0 + t2) + (t1 + t3),            X[k + N/2]  = (t0 + t2) - (t1 + t3),
+//   X[k + N/4] = (t0 - t2) + w (t1 - t3),    X[k + 3N/4] = (t0 - t2) - w (t1 - t3),
+// w = W_4 = -i (forward) or +i (inverse): three twiddle products per four outputs
+// instead of the four of two radix-2 levels.
+template <int N, int DIR, int K, int R>
+__device__ __forceinline__ float2 tw_r4(float2 v) {
+  constexpr int m = R * K;  // exponent of W_N, 0 <= m < 3N/4
+  if constexpr (m == 0) {
+    return v;
+  } else if constexpr (4 * m == N) {  // W = -i (forward) or +i (inverse)
+    if constexpr (DIR < 0) return make_float2(v.y, -v.x);
+    else return make_float2(-v.y, v.x);
+  } else if constexpr (2 * m == N) {  // W = -1
+    return make_float2(-v.x, -v.y);
+  } else {
+    constexpr float wr = Tw<N, m>::re;
+    constexpr float wi = DIR < 0 ? Tw<N, m>::im : -Tw<N, m>::im;
+    return make_float2(v.x * wr - v.y * wi, v.x * wi + v.y * wr);
+  }
+}
+
+template <int N, int DIR, int K>
+__device__ __forceinline__ void dft4_bfly(float2 (&x)[N], const float2 (&e0)[N / 4],
+                                          const float2 (&e1)[N / 4], const float2 (&e2)[N / 4],
+                                          const float2 (&e3)[N / 4]) {
+  constexpr int M = N / 4;
+  const float2 t0 = e0[K];
+  const float2 t1 = tw_r4<N, DIR, K, 1>(e1[K]);
+  const float2 t2 = tw_r4<N, DIR, K, 2>(e2[K]);
+  const float2 t3 = tw_r4<N, DIR, K, 3>(e3[K]);
+  const float2 a = cadd(t0, t2), b = csub(t0, t2), c = cadd(t1, t3), d = csub(t1, t3);
+  // w d with w = -i (forward) or +i (inverse)
+  const float2 wd = DIR < 0 ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);
+  x[K] = cadd(a, c);
+  x[K + 2 * M] = csub(a, c);
+  x[K + M] = cadd(b, wd);
+  x[K + 3 * M] = csub(b, wd);
+}
+
+template <int N, int DIR, int... K>
+__device__ __forceinline__ void dft4_combine(float2 (&x)[N], const float2 (&e0)[N / 4],
+                                             const float2 (&e1)[N / 4], const float2 (&e2)[N / 4],
+                                             const float2 (&e3)[N / 4],
+                                             std::integer_sequence<int, K...>) {
+  (dft4_bfly<N, DIR, K>(x, e0, e1, e2, e3), ...);
+}
+
 template <int N, int DIR>
 struct Dft {
   static __device__ __forceinline__ void run(float2 (&x)[N]) {
-    if constexpr (N % 3 == 0) {
+    if constexpr (N % 4 == 0 && N >= 16) {
+      constexpr int M = N / 4;
+      float2 e0[M], e1[M], e2[M], e3[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        e0[i] = x[4 * i];
+        e1[i] = x[4 * i + 1];
+        e2[i] = x[4 * i + 2];
+        e3[i] = x[4 * i + 3];
+      }
+      Dft<M, DIR>::run(e0);
+      Dft<M, DIR>::run(e1);
+      Dft<M, DIR>::run(e2);
+      Dft<M, DIR>::run(e3);
+      dft4_combine<N, DIR>(x, e0, e1, e2, e3, std::make_integer_sequence<int, M>{});
+    } else if constexpr (N % 3 == 0) {
       constexpr int M = N / 3;
       float2 e0[M], e1[M], e2[M];
 #pragma unroll

@@ -22,6 +22,18 @@ namespace dev {
 
 constexpr int kMaxGroup = 256;  // filters per launch whose thresholds travel by value
 
+// Minimum resident CTAs per SM requested from the compiler for the persistent
+// filter-loop kernels (register caps); compile-time tunables.
+#ifndef SL_MINB_COLF
+#define SL_MINB_COLF 1
+#endif
+#ifndef SL_MINB_COLI
+#define SL_MINB_COLI 1
+#endif
+#ifndef SL_MINB_ROW
+#define SL_MINB_ROW 1
+#endif
+
 // Concatenated twiddle tables, one per line length L = 8..1024:
 // g_twiddle[twiddle_offset(L) + kb * A + a] = exp(-2 pi i a kb / L).
 // Filled once per device from FP64 values by the host (this header is compiled in
@@ -195,7 +207,7 @@ __device__ __forceinline__ void cp_async_block(void* dst, const void* src, int b
 // the other shared-memory stage with cp.async, so global-memory latency overlaps
 // with the FFT. Output as COL_FWD_FILT: out[s] = IFFT_0(in * psi[j0 + s]).
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T) k_col_fwd_pipe(ColArgs p) {
+__global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLF) k_col_fwd_pipe(ColArgs p) {
   using G = Geo<L>;
   constexpr int A = G::A, B = G::B, TC = G::TC, T = G::T, XS = G::XS;
   constexpr int TILE = L * TC;  // elements of one tile
@@ -467,7 +479,7 @@ struct RowPipe {
 };
 
 template <int L, int MODE, int PAIRS>
-__global__ void __launch_bounds__(PAIRS * Split<L>::A)
+__global__ void __launch_bounds__(PAIRS * Split<L>::A, SL_MINB_ROW)
     k_row_pipe(RowArgs p, int nslots, int NPp, int stage_bytes) {
   using RP = RowPipe<L, MODE, PAIRS>;
   constexpr int A = RP::A, B = RP::B, T = RP::T, LS = RP::LS;
@@ -627,7 +639,7 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A)
 // pairs of its items' filters through two shared-memory stages and accumulates
 // psi_j * FFT_0(Z_j) in registers, writing one partial per item.
 template <int L>
-__global__ void __launch_bounds__(Geo<L>::T) k_col_inv_pipe(ColArgs p) {
+__global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLI) k_col_inv_pipe(ColArgs p) {
   using G = Geo<L>;
   constexpr int A = G::A, B = G::B, TC = G::TC, T = G::T, XS = G::XS;
   constexpr int TILE = L * TC;
