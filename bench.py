@@ -151,6 +151,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------ our arm ---
 
+# FP32 peak from the unit counts and clocks: 148 SMs x 128 FP32 lanes x 2 flops (FMA)
+# x 2.032 GHz maximum SM clock
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def alu_roofline(R: int, N: int, ms: float) -> dict:
+    """The FP32 co-bound of the step: one real FFT costs about 2.5 N log2 N flops and a
+    forward + inverse takes 2 (R + 1) of them (the signal's and one per filter each
+    way), i.e. 5 (R + 1) N log2 N."""
+    import math
+    flops = 5.0 * (R + 1) * N * math.log2(N)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "flops_per_step": flops, "achieved": achieved,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+
+
 def max_over_ranks(ms: float, ws: int, device: str) -> float:
     """The slowest rank's time: every rank contributes its own, all get the maximum
     (NCCL on the GPUs; gloo with device="cpu")."""
@@ -300,6 +317,7 @@ def run_ours(args):
                      "ms_per_launch": t_ms / n_l},
         "roofline_step": {"alg_bytes": alg_step, "achieved_GBps": alg_step / (ms_step * 1e-3) / 1e9,
                           "frac": alg_step / (ms_step * 1e-3) / 1e9 / peak},
+        "roofline_alu": alu_roofline(R, N, ms_step),
         "kernels": kernels,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "e2e": {"value": R * N * n_gpus / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,

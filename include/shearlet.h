@@ -17,6 +17,8 @@
  *              one contiguous plane/volume per filter, filter 0 (the lowpass) first.
  *   Memory:    unless a name ends in _host, data pointers are DEVICE pointers on the
  *              bank's device, owned by the caller; the library never frees them.
+ *              Signal and coefficient arrays must be 16-byte aligned (cudaMalloc and
+ *              torch allocations are); SL_EINVAL otherwise.
  *              The library owns the bank, its filters and its scratch memory.
  *   Streams:   `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *              stream). Calls are asynchronous on that stream; the caller
@@ -325,6 +327,12 @@ int sl_mlp_num_params(const sl_mlp* mlp);
 /* Host <-> device copies of the flat parameters; set also resets Adam's state. */
 sl_status sl_mlp_set_params(sl_mlp* mlp, const float* host);
 sl_status sl_mlp_get_params(const sl_mlp* mlp, float* host);
+/* Checkpoint and resume: write the parameters and Adam's state (moments and step
+ * count) to a file, or read them back into an MLP of the same bank shape (ndim, R;
+ * SL_EINVAL for another shape, a missing file or a truncated one). Training that
+ * resumes from a checkpoint takes exactly the steps it would have taken. */
+sl_status sl_mlp_save(const sl_mlp* mlp, const char* path);
+sl_status sl_mlp_load(sl_mlp* mlp, const char* path);
 /* Gradients of the loss over the n samples idx (DEVICE int32 flat indices
  * q = j * N + m with j >= 1; n a positive multiple of 128) of the DEVICE coefficient
  * stacks noisy and clean [R][dims], copied to grad_host[num_params] and *loss_host

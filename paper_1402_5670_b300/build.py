@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libshearlet.so")
 SOURCES = ["shearlet.cu", "bank_host.cpp", "mlp.cu"]
 HEADERS = ["fft_core.cuh", "kernels2d.cuh", "kernels3d.cuh", "kernels_cluster.cuh", "kernels_tc.cuh",
+           "kernels_roww.cuh",
            "bank_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

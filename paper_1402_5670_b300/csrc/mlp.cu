@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -679,6 +681,54 @@ sl_status sl_mlp_get_params(const sl_mlp* M, float* host) {
   if (!M || !host) return mfail(SL_EINVAL, "NULL argument");
   if (cudaMemcpy(host, M->prm, M->P * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
     return mfail(SL_ECUDA, "cudaMemcpy");
+  return SL_OK;
+}
+
+// Checkpoint file: an 8-byte magic, four int32 (ndim, R, P, Adam step t), then the
+// parameters, Adam's first and second moments (P float32 each), little endian.
+static const char kCkptMagic[8] = {'S', 'L', 'M', 'L', 'P', '0', '0', '1'};
+
+sl_status sl_mlp_save(const sl_mlp* M, const char* path) {
+  if (!M || !path) return mfail(SL_EINVAL, "NULL argument");
+  std::vector<float> buf((size_t)3 * M->P);
+  if (cudaMemcpy(buf.data(), M->prm, M->P * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + M->P, M->m, M->P * sizeof(float), cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      cudaMemcpy(buf.data() + 2 * (size_t)M->P, M->v, M->P * sizeof(float),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mfail(SL_ECUDA, "cudaMemcpy");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return mfail(SL_EINVAL, std::string("cannot open ") + path + " for writing");
+  const int32_t hdr[4] = {M->ndim, M->R, M->P, M->t};
+  const bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 4, f) == 4 &&
+                  std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  if (std::fclose(f) != 0 || !ok) return mfail(SL_EINVAL, std::string("writing ") + path + " failed");
+  return SL_OK;
+}
+
+sl_status sl_mlp_load(sl_mlp* M, const char* path) {
+  if (!M || !path) return mfail(SL_EINVAL, "NULL argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return mfail(SL_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t hdr[4];
+  std::vector<float> buf((size_t)3 * M->P);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+            std::fread(hdr, 4, 4, f) == 4;
+  if (ok && (hdr[0] != M->ndim || hdr[1] != M->R || hdr[2] != M->P || hdr[3] < 0)) {
+    std::fclose(f);
+    return mfail(SL_EINVAL, "checkpoint was written for another bank shape");
+  }
+  ok = ok && std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return mfail(SL_EINVAL, std::string(path) + " is not a complete MLP checkpoint");
+  if (cudaMemcpy(M->prm, buf.data(), M->P * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(M->m, buf.data() + M->P, M->P * sizeof(float), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(M->v, buf.data() + 2 * (size_t)M->P, M->P * sizeof(float),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return mfail(SL_ECUDA, "cudaMemcpy");
+  M->t = hdr[3];
   return SL_OK;
 }
 

@@ -21,6 +21,7 @@
 #include "kernels3d.cuh"
 #include "kernels_cluster.cuh"
 #include "kernels_tc.cuh"
+#include "kernels_roww.cuh"
 
 using sl::dev::ColArgs;
 using sl::dev::RowArgs;
@@ -234,6 +235,28 @@ static cudaError_t launch_row_pipe_t(int slots, int L0, int NPp, cudaStream_t st
                       [&]() { k<<<grid, T, smem, st>>>(a, slots, NPp, stage); });
 }
 
+// Warp-pipelined row passes (kernels_roww.cuh) for rows of 512 and 1024 points; used
+// for the single-signal passes (one warp per CTA: the few row pairs of one image
+// spread over many SMs with both FFT passes on all lanes). For the filter loop the
+// CTA-wide pipeline (k_row_pipe) measured as fast or faster on B300.
+template <int L, int MODE, int W>
+static cudaError_t launch_row_warp_t(int slots, int L0, int NPp, cudaStream_t st,
+                                     const RowArgs& a) {
+  constexpr int T = 32 * W;
+  auto k = sl::dev::k_row_warp<L, MODE, W>;
+  const int stage = MODE == sl::dev::ROW_R2C ? 2 * L * 4 : 2 * NPp * 8;
+  const int smem = W * (2 * stage + sl::dev::roww_exchange_bytes<L>());
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int items = slots * (L0 / 2);
+  const int ctas = (items + W - 1) / W;
+  const int grid = std::min(ctas, persistent_grid(k, T, smem, 6000 + 10 * L + 100 * W + MODE));
+  static const char* names[3] = {"row_r2c", "row_c2r", "row_roundtrip"};
+  static const char* names1[3] = {"row_r2c_signal", "row_c2r_signal", "row_roundtrip"};
+  return timed_launch(slots == 1 ? names1[MODE] : names[MODE], st,
+                      [&]() { k<<<grid, T, smem, st>>>(a, slots, NPp, stage); });
+}
+
 template <int MODE>
 static cudaError_t launch_row_pipe(int L, int slots, int L0, int NPp, cudaStream_t st,
                                    const RowArgs& a) {
@@ -341,24 +364,30 @@ static cudaError_t launch_row_p(dim3 grid, cudaStream_t st, const RowArgs& a) {
 }
 
 template <int L, int MODE>
-static cudaError_t launch_row_t(int slots, int L0, cudaStream_t st, const RowArgs& a) {
+static cudaError_t launch_row_t(int slots, int L0, int NPp, cudaStream_t st, const RowArgs& a) {
   constexpr int W = sl::dev::col_tile_of(L);
+  if constexpr (L == 512 || L == 1024) {
+    // one row pair per one-warp CTA, both passes on all 32 lanes
+    if (slots == 1 && MODE != sl::dev::ROW_RT)
+      return launch_row_warp_t<L, MODE, 1>(1, L0, NPp, st, a);
+  }
   if (slots == 1) return launch_row_p<L, MODE, 1>(dim3(L0 / 2, 1), st, a);
   return launch_row_p<L, MODE, W>(dim3((L0 / 2 + W - 1) / W, slots), st, a);
 }
 
 template <int MODE>
-static cudaError_t launch_row(int L, int slots, int L0, cudaStream_t st, const RowArgs& a) {
+static cudaError_t launch_row(int L, int slots, int L0, int NPp, cudaStream_t st,
+                              const RowArgs& a) {
   switch (L) {
-    case 8: return launch_row_t<8, MODE>(slots, L0, st, a);
-    case 16: return launch_row_t<16, MODE>(slots, L0, st, a);
-    case 32: return launch_row_t<32, MODE>(slots, L0, st, a);
-    case 64: return launch_row_t<64, MODE>(slots, L0, st, a);
-    case 128: return launch_row_t<128, MODE>(slots, L0, st, a);
-    case 256: return launch_row_t<256, MODE>(slots, L0, st, a);
-    case 512: return launch_row_t<512, MODE>(slots, L0, st, a);
-    case 1024: return launch_row_t<1024, MODE>(slots, L0, st, a);
-    case 384: return launch_row_t<384, MODE>(slots, L0, st, a);
+    case 8: return launch_row_t<8, MODE>(slots, L0, NPp, st, a);
+    case 16: return launch_row_t<16, MODE>(slots, L0, NPp, st, a);
+    case 32: return launch_row_t<32, MODE>(slots, L0, NPp, st, a);
+    case 64: return launch_row_t<64, MODE>(slots, L0, NPp, st, a);
+    case 128: return launch_row_t<128, MODE>(slots, L0, NPp, st, a);
+    case 256: return launch_row_t<256, MODE>(slots, L0, NPp, st, a);
+    case 512: return launch_row_t<512, MODE>(slots, L0, NPp, st, a);
+    case 1024: return launch_row_t<1024, MODE>(slots, L0, NPp, st, a);
+    case 384: return launch_row_t<384, MODE>(slots, L0, NPp, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -860,6 +889,13 @@ sl_status sl_bank_filters_f32(const sl_bank* b, float* out) {
 
 // --------------------------------------------------------------- transforms ---
 
+// Device arrays are read and written with 16-byte vector and asynchronous copies.
+static bool a16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+static sl_status check_aligned(const void* p, const void* q) {
+  if (!a16(p) || !a16(q)) return fail(SL_EINVAL, "device arrays must be 16-byte aligned");
+  return SL_OK;
+}
+
 static sl_status check_call(const sl_bank* b) {
   if (!b) return fail(SL_EINVAL, "bank is NULL");
   if (b->device < 0) return fail(SL_EINVAL, "host-only bank (built with device = -1)");
@@ -937,7 +973,8 @@ static sl_status last_axes(const Plan& P, RowArgs& ra, int slots, cudaStream_t s
     if (slots > 1 && L0 / 2 >= pairs && (L0 / 2) % pairs == 0)
       return launched(launch_row_pipe<MODE>((int)s.dims[1], slots, L0, P.ntiles * P.TC, st, ra),
                       "row pass");
-    return launched(launch_row<MODE>((int)s.dims[1], slots, L0, st, ra), "row pass");
+    return launched(launch_row<MODE>((int)s.dims[1], slots, L0, P.ntiles * P.TC, st, ra),
+                    "row pass");
   }
   return launched(launch_plane<MODE>((int)s.dims[1], (int)s.dims[2], dim3(L0, slots), st, ra),
                   "plane pass");
@@ -1173,6 +1210,7 @@ extern "C" {
 sl_status sl_forward(const sl_bank* b, const float* x, float* coeffs, void* stream) {
   SL_TRY(check_call(b));
   if (!x || !coeffs) return fail(SL_EINVAL, "x or coeffs is NULL");
+  SL_TRY(check_aligned(x, coeffs));
   if (b->cl) return cl_forward(b, x, coeffs, (cudaStream_t)stream);
   return forward_plan(plan_of(b), x, coeffs, (cudaStream_t)stream);
 }
@@ -1180,6 +1218,7 @@ sl_status sl_forward(const sl_bank* b, const float* x, float* coeffs, void* stre
 sl_status sl_adjoint(const sl_bank* b, const float* coeffs, float* x, void* stream) {
   SL_TRY(check_call(b));
   if (!x || !coeffs) return fail(SL_EINVAL, "x or coeffs is NULL");
+  SL_TRY(check_aligned(x, coeffs));
   if (b->cl) return cl_backward(b, coeffs, x, false, (cudaStream_t)stream);
   return backward(plan_of(b), coeffs, x, false, (cudaStream_t)stream);
 }
@@ -1187,6 +1226,7 @@ sl_status sl_adjoint(const sl_bank* b, const float* coeffs, float* x, void* stre
 sl_status sl_inverse(const sl_bank* b, const float* coeffs, float* x, void* stream) {
   SL_TRY(check_call(b));
   if (!x || !coeffs) return fail(SL_EINVAL, "x or coeffs is NULL");
+  SL_TRY(check_aligned(x, coeffs));
   if (b->cl) return cl_backward(b, coeffs, x, true, (cudaStream_t)stream);
   return backward(plan_of(b), coeffs, x, true, (cudaStream_t)stream);
 }
@@ -1195,6 +1235,7 @@ sl_status sl_threshold(const sl_bank* b, float* coeffs, float sigma, const float
                        void* stream) {
   SL_TRY(check_call(b));
   if (!coeffs || !K) return fail(SL_EINVAL, "coeffs or K is NULL");
+  SL_TRY(check_aligned(coeffs, coeffs));
   if (!(sigma >= 0.f) || !std::isfinite(sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
   for (int j = 0; j < b->spec.J; ++j)
     if (!std::isfinite(K[j])) return fail(SL_EINVAL, "K must be finite");
@@ -1221,6 +1262,7 @@ sl_status sl_denoise(const sl_bank* b, const float* noisy, float* out, float sig
                      const float* K, void* stream) {
   SL_TRY(check_call(b));
   if (!noisy || !out || !K) return fail(SL_EINVAL, "noisy, out or K is NULL");
+  SL_TRY(check_aligned(noisy, out));
   if (!(sigma >= 0.f) || !std::isfinite(sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
   return denoise_plan(plan_of(b), noisy, out, sigma, K, (cudaStream_t)stream);
 }
@@ -1565,9 +1607,12 @@ static sl_status batch_check_io(const sl_batch* B, int op, const BatchIO& io) {
   const bool need_x = op != BOP_INV, need_c = op != BOP_DENOISE, need_y = op != BOP_FWD;
   if ((need_x && !io.x) || (need_c && !io.c) || (need_y && !io.y))
     return fail(SL_EINVAL, "a pointer array is NULL");
-  for (int i = 0; i < B->n; ++i)
+  for (int i = 0; i < B->n; ++i) {
     if ((need_x && !io.x[i]) || (need_c && !io.c[i]) || (need_y && !io.y[i]))
       return fail(SL_EINVAL, "image " + std::to_string(i) + ": NULL data pointer");
+    if ((need_x && !a16(io.x[i])) || (need_c && !a16(io.c[i])) || (need_y && !a16(io.y[i])))
+      return fail(SL_EINVAL, "image " + std::to_string(i) + ": data not 16-byte aligned");
+  }
   if (op == BOP_DENOISE) {
     if (!io.K) return fail(SL_EINVAL, "K is NULL");
     if (!(io.sigma >= 0.f) || !std::isfinite(io.sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
@@ -1856,6 +1901,8 @@ extern "C" sl_status sl_forward_noalloc(const sl_bank* b, const float* psi, cons
                                         float* coeffs, void* stream) {
   if (!b) return fail(SL_EINVAL, "bank is NULL");
   if (!psi || !x || !coeffs) return fail(SL_EINVAL, "psi, x or coeffs is NULL");
+  SL_TRY(check_aligned(x, coeffs));
+  SL_TRY(check_aligned(psi, psi));
   const int64_t cap = (int64_t)(SL_NOALLOC_SCRATCH_BYTES / sizeof(float2));
   if (2 * b->Nhp > cap)
     return fail(SL_ENOTSUP, "sl_forward_noalloc: the signal's spectrum plus one filter's "

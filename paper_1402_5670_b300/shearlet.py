@@ -74,6 +74,8 @@ SIGNATURES = {
     "sl_mlp_apply": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp]),
     "sl_mlp_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _vp]),
     "sl_mlp_last_error": (ctypes.c_char_p, []),
+    "sl_mlp_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "sl_mlp_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "sl_error_stats": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _c_double_p, _vp]),
     "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sl_profile_reset": (ctypes.c_int, []),
@@ -401,6 +403,13 @@ class MLP:
         _mcheck(lib().sl_mlp_get_params(self.handle, out.ctypes.data_as(_c_float_p)),
                 "sl_mlp_get_params")
         return out
+
+    def save(self, path: str) -> None:
+        """Checkpoint: parameters and Adam's state."""
+        _mcheck(lib().sl_mlp_save(self.handle, os.fsencode(path)), "sl_mlp_save")
+
+    def load(self, path: str) -> None:
+        _mcheck(lib().sl_mlp_load(self.handle, os.fsencode(path)), "sl_mlp_load")
 
     def _sample(self, idx):
         import torch

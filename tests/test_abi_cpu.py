@@ -117,3 +117,4 @@ def test_library_bank_matches_oracle_at_384():
         assert np.max(np.abs(b.eval_f64(j) - s.psi_hat(j)[:, :193])) <= 1e-12
     assert abs(b.A - s.A) <= 1e-12
     b.close()
+

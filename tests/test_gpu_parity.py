@@ -260,3 +260,20 @@ def test_error_stats_kernel_matches_numpy():
     assert st["max_abs_ref"] == np.max(np.abs(xd))
     assert abs(st["sum_sq_err"] - np.sum((yd - xd) ** 2)) <= 1e-12 * np.sum((yd - xd) ** 2)
     assert abs(st["psnr"] - O.psnr(xd, yd)) < 1e-9
+
+
+def test_misaligned_arrays_are_rejected_on_the_host():
+    """Device arrays are accessed with 16-byte vector and asynchronous copies; a
+    misaligned pointer is refused with SL_EINVAL before any kernel runs."""
+    from paper_1402_5670_b300 import shearlet as S
+    dims = (64, 64)
+    b = bank(dims, 2, (1, 1))
+    buf = torch.zeros(b.N + 4, device="cuda")
+    C = torch.zeros((b.R,) + dims, device="cuda")
+    st = S.lib().sl_forward(b.handle, buf.data_ptr() + 4, C.data_ptr(), None)
+    assert S.STATUS[st] == "SL_EINVAL"
+    assert "aligned" in S.lib().sl_last_error().decode()
+    cbuf = torch.zeros(b.R * b.N + 4, device="cuda")
+    st = S.lib().sl_inverse(b.handle, cbuf.data_ptr() + 8, buf.data_ptr(), None)
+    assert S.STATUS[st] == "SL_EINVAL"
+    torch.cuda.synchronize()

@@ -201,3 +201,39 @@ def test_learned_shrinkage_beats_hard_thresholding():
     print("PSNR gain of learned over hard thresholding (dB):", np.round(gains, 2))
     assert min(gains) > 0.0
     assert float(np.mean(gains)) > 0.1
+
+
+@pytest.mark.gpu
+def test_checkpoint_resume(tmp_path):
+    """Save after 3 Adam steps, keep training; a fresh MLP loaded from the checkpoint
+    holds the same parameters and continues to the same place (up to the summation
+    order of the gradient reduction); a checkpoint of another shape is refused."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5670_b300.shearlet import MLP, Bank, ShearletError
+    dims, J, sl = (64, 64), 2, (1, 1)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 6)
+    r = np.random.default_rng(7)
+    idxs = [torch.from_numpy(r.integers(b.N, b.R * b.N, 1024).astype(np.int32)).cuda()
+            for _ in range(5)]
+    for i in range(3):
+        mlp.train_step(Cn, Cc, 20.0, idxs[i], 1e-3)
+    ck = str(tmp_path / "mlp.ckpt")
+    mlp.save(ck)
+    saved = mlp.get_params()
+    for i in range(3, 5):
+        mlp.train_step(Cn, Cc, 20.0, idxs[i], 1e-3)
+    after = mlp.get_params()
+    m2 = MLP(b)
+    m2.load(ck)
+    assert np.array_equal(m2.get_params(), saved)
+    for i in range(3, 5):
+        m2.train_step(Cn, Cc, 20.0, idxs[i], 1e-3)
+    assert np.max(np.abs(m2.get_params() - after)) <= 1e-5 * np.max(np.abs(after))
+    assert not np.allclose(after, saved)
+    b2 = Bank((32, 32), 1, (0,), device=0)
+    m3 = MLP(b2)
+    with pytest.raises(ShearletError):
+        m3.load(ck)
+    with pytest.raises(ShearletError):
+        m3.load(str(tmp_path / "missing.ckpt"))
