@@ -23,7 +23,8 @@ namespace dev {
 constexpr int kMaxGroup = 256;  // filters per launch whose thresholds travel by value
 
 // Minimum resident CTAs per SM requested from the compiler for the persistent
-// filter-loop kernels (register caps); compile-time tunables.
+// filter-loop kernels (register caps; the row pipeline's shared memory allows four
+// CTAs per SM up to 512-point rows, two for 1024); compile-time tunables.
 #ifndef SL_MINB_COLF
 #define SL_MINB_COLF 1
 #endif
@@ -31,7 +32,7 @@ constexpr int kMaxGroup = 256;  // filters per launch whose thresholds travel by
 #define SL_MINB_COLI 1
 #endif
 #ifndef SL_MINB_ROW
-#define SL_MINB_ROW 1
+#define SL_MINB_ROW 4
 #endif
 
 // Concatenated twiddle tables, one per line length L = 8..1024:
@@ -67,8 +68,10 @@ struct Geo {
 struct TileMap {
   int L0;   // pencil length n0
   int lg;   // log2(TC)
-  __device__ __forceinline__ int64_t at(int k0, int p) const {
-    return ((int64_t)((p >> lg) * L0 + k0) << lg) + (p & ((1 << lg) - 1));
+  // 32-bit arithmetic: a spectrum holds fewer than 2^31 elements (N <= 2^31 is checked
+  // when the bank is built)
+  __device__ __forceinline__ int at(int k0, int p) const {
+    return (((p >> lg) * L0 + k0) << lg) + (p & ((1 << lg) - 1));
   }
 };
 __device__ __forceinline__ int tm_tc(const TileMap& t) { return 1 << t.lg; }
@@ -232,6 +235,10 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLF) k_col_fwd_pipe(ColArg
     cp_async_commit();
   };
 
+  float2 twr[B];  // this thread's inter-pass twiddles, the same for every item
+#pragma unroll
+  for (int kb = 1; kb < B; ++kb) twr[kb] = tw[kb * A + a];
+
   int item = blockIdx.x;
   issue(item, 0);
   issue(item + gridDim.x, 1);
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLF) k_col_fwd_pipe(ColArg
     }
     Dft<B, 1>::run(v);
 #pragma unroll
-    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a]);
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], twr[kb]);
 #pragma unroll
     for (int kb = 0; kb < B; ++kb) ex[kb * XS + a * TC + line] = v[kb];
     __syncthreads();                        // stage and exchange inputs consumed
@@ -479,7 +486,7 @@ struct RowPipe {
 };
 
 template <int L, int MODE, int PAIRS>
-__global__ void __launch_bounds__(PAIRS * Split<L>::A, SL_MINB_ROW)
+__global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_ROW)
     k_row_pipe(RowArgs p, int nslots, int NPp, int stage_bytes) {
   using RP = RowPipe<L, MODE, PAIRS>;
   constexpr int A = RP::A, B = RP::B, T = RP::T, LS = RP::LS;
@@ -507,19 +514,28 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, SL_MINB_ROW)
           cp_async16(dst + o, reinterpret_cast<const char*>(src) + o);
       } else {
         const float2* src = p.in_half + (int64_t)slot * p.in_stride;
-        const int tc = tm_tc(tm);
-        const int chunks = tc / 2;  // 16-byte chunks per tile run
-        const int per_row = nrun * chunks;
-        for (int c = tid; c < 2 * PAIRS * per_row; c += T) {
-          const int rr = c / per_row, rem = c % per_row;
-          const int t = rem / chunks, ch = rem % chunks;
-          const float2* g = src + (((int64_t)t * tm.L0 + r0 + rr) << tm.lg) + 2 * ch;
-          cp_async16(dst + ((int64_t)rr * NPp + t * tc + 2 * ch) * 8, g);
+        // tile run t of row r0 + rr is TC = 2^lg elements at ((t L0 + r0 + rr) << lg):
+        // 2^(lg-1) chunks of 16 bytes; no divisions in the copy loop
+        const int lgc = tm.lg - 1;
+        const int per_row = nrun << lgc;
+        for (int rr = 0; rr < 2 * PAIRS; ++rr) {
+          const float2* srow = src + ((int64_t)(r0 + rr) << tm.lg);
+          unsigned char* drow = dst + (int64_t)rr * NPp * 8;
+          for (int c = tid; c < per_row; c += T) {
+            const int t = c >> lgc, ch2 = 2 * (c & ((1 << lgc) - 1));
+            cp_async16(drow + (((int64_t)t << tm.lg) + ch2) * 8,
+                       srow + ((int64_t)t * tm.L0 << tm.lg) + ch2);
+          }
         }
       }
     }
     cp_async_commit();
   };
+
+  // this thread's inter-pass twiddles are the same for every item
+  float2 twr[B];
+#pragma unroll
+  for (int kb = 1; kb < B; ++kb) twr[kb] = tw[kb * A + a1];
 
   int item = blockIdx.x;
   issue(item, 0);
@@ -547,7 +563,7 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, SL_MINB_ROW)
       }
       Dft<B, 1>::run(v);
 #pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a1]);
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], twr[kb]);
 #pragma unroll
       for (int kb = 0; kb < B; ++kb) sm[line1 * LS + kb * (A + 1) + a1] = v[kb];
       __syncthreads();
@@ -604,7 +620,7 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, SL_MINB_ROW)
       issue(item + 2 * gridDim.x, stage);
       Dft<B, -1>::run(v);
 #pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a1]);
+      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], twr[kb]);
 #pragma unroll
       for (int kb = 0; kb < B; ++kb) sm[line1 * LS + kb * (A + 1) + a1] = v[kb];
     }
