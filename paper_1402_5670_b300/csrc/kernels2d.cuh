@@ -290,8 +290,9 @@ __global__ void __launch_bounds__(256) k_reduce_parts(const float2* __restrict__
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
        i += (int64_t)gridDim.x * blockDim.x) {
     float4 s = p4[i];
-    for (int q = 1; q < nparts; ++q) {
-      const float4 t = p4[q * s4 + i];
+#pragma unroll 8
+    for (int q = 1; q < nparts; ++q) {  // loads independent of the sum: issued ahead
+      const float4 t = __ldg(p4 + q * s4 + i);
       s.x += t.x;
       s.y += t.y;
       s.z += t.z;
@@ -573,14 +574,17 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) res[aa] = sm[line2 * LS + kb2 * (A + 1) + aa];
         Dft<A, 1>::run(res);
+        if (p.use_thr) {  // uniform branch: no per-value predication when unused
 #pragma unroll
-        for (int ka = 0; ka < A; ++ka) {
-          float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
-          if (p.use_thr) {
+          for (int ka = 0; ka < A; ++ka) {
+            float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
             if (fabsf(c0) < thr) c0 = 0.f;
             if (fabsf(c1) < thr) c1 = 0.f;
+            res[ka] = make_float2(c0, c1);
           }
-          res[ka] = make_float2(c0, c1);
+        } else {
+#pragma unroll
+          for (int ka = 0; ka < A; ++ka) res[ka] = cscale(res[ka], p.scale);
         }
       }
       if constexpr (MODE == ROW_C2R) {
