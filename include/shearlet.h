@@ -187,11 +187,14 @@ sl_status sl_denoise(const sl_bank* bank, const float* noisy, float* out, float 
  * End-to-end round trip from HOST memory: copies x_host[dims] to the device,
  * runs sl_forward into library-owned coefficient memory, then sl_inverse, and
  * copies the reconstruction back to y_host[dims]. Host arrays should be pinned
- * (cudaHostAlloc) for asynchronous copies; with pinned buffers the copies and
- * kernels are captured into a CUDA graph on the first call with a given pair of
- * host pointers and replayed by one graph launch afterwards (the bank's round-trip
- * state is shared: do not run two round trips of one bank at once). Returns after
- * queuing; synchronise the
+ * (cudaHostAlloc) for asynchronous copies; with pinned buffers the work is captured
+ * into a CUDA graph on the first call with a given pair of host pointers and
+ * replayed by one graph launch afterwards (the bank's round-trip state is shared:
+ * do not run two round trips of one bank at once). Pinned buffers that the device
+ * can address (mapped, as cudaHostAlloc memory is under unified addressing) and
+ * that are 16-byte aligned are read by the first kernel and written by the last one
+ * directly over the host link, with no separate copy (general kernel path); other
+ * pinned buffers go through cudaMemcpyAsync. Returns after queuing; synchronise the
  * stream before reading y_host.
  */
 sl_status sl_fwdinv_host(const sl_bank* bank, const float* x_host, float* y_host,

@@ -1299,11 +1299,21 @@ sl_status sl_fwdinv_host(const sl_bank* cb, const float* x_host, float* y_host, 
                       ax.type == cudaMemoryTypeHost && ay.type == cudaMemoryTypeHost;
   cudaGetLastError();
   if (!pinned || g_prof_on) return issue(st);
+  // Pinned buffers that the device can address (mapped; 16-byte aligned) are read
+  // and written by the first and last kernels themselves over the host link,
+  // without a separate copy (general path only).
+  const float* xd = static_cast<const float*>(ax.devicePointer);
+  float* yd = static_cast<float*>(ay.devicePointer);
+  const bool mapped = !b->cl && xd && yd && a16(xd) && a16(yd);
+  auto issue_mapped = [&](cudaStream_t s) -> sl_status {
+    SL_TRY(sl_forward(b, xd, b->e2e_c, s));
+    return sl_inverse(b, b->e2e_c, yd, s);
+  };
   if (!b->e2e_graph || b->e2e_key[0] != x_host || b->e2e_key[1] != y_host) {
     if (!b->e2e_cap) SL_CUDA(cudaStreamCreateWithFlags(&b->e2e_cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     SL_CUDA(cudaStreamBeginCapture(b->e2e_cap, cudaStreamCaptureModeRelaxed));
-    const sl_status s = issue(b->e2e_cap);
+    const sl_status s = mapped ? issue_mapped(b->e2e_cap) : issue(b->e2e_cap);
     cudaError_t e = cudaStreamEndCapture(b->e2e_cap, &g);
     if (s != SL_OK) {
       if (g) cudaGraphDestroy(g);
