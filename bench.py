@@ -322,7 +322,7 @@ def run_ours(args):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "e2e": {"value": R * N * n_gpus / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
-                "api": "sl_fwdinv_host (pinned host buffers)"},
+                "api": "sl_fwdinv_host (pinned, mapped host buffers: the first kernel reads the input and the last writes the result over the host link)"},
         "clocks": clk,
     }
     if n_gpus == 1 and not args.no_extras:
