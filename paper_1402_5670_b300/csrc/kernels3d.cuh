@@ -7,7 +7,9 @@
 namespace sl {
 namespace dev {
 
-constexpr int kPlaneThreads = 512;
+// 17 warps: the plane phases have 1040, 520, 1024, 512 and 4160 work items at 128 x 128,
+// so 544 threads take the column FFT in two rounds and its second pass in one.
+constexpr int kPlaneThreads = 544;
 
 template <int L1, int L2>
 struct PlaneGeom {
@@ -74,7 +76,19 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
 
   if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
     const float2* in = p.in_half + (int64_t)slot * p.in_stride;
-    for (int i = tid; i < G::HALF; i += kPlaneThreads) P[i] = in[p.tm.at(i0, i)];
+    // all of this thread's loads issued before any of them is used
+    constexpr int NIT = (G::HALF + kPlaneThreads - 1) / kPlaneThreads;
+    float2 ld[NIT];
+#pragma unroll
+    for (int r = 0; r < NIT; ++r) {
+      const int i = tid + r * kPlaneThreads;
+      ld[r] = i < G::HALF ? in[p.tm.at(i0, i)] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < NIT; ++r) {
+      const int i = tid + r * kPlaneThreads;
+      if (i < G::HALF) P[i] = ld[r];
+    }
     __syncthreads();
     plane_col_fft<L1, NH, 1>(P, W, P);
     // rows (2q, 2q+1): complex inverse DFT of the Hermitian-extended pair
@@ -138,20 +152,33 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
     const float* inr = nullptr;
     if constexpr (MODE == ROW_R2C)
       inr = p.in_real + (int64_t)slot * p.in_stride + (int64_t)i0 * (L1 * L2);
-    for (int it = tid; it < PAIRS * A; it += kPlaneThreads) {
+    // this thread's items (a, q): all their input values are loaded before the first
+    // transform, so the global-memory latency is paid once
+    constexpr int NI = (PAIRS * A + kPlaneThreads - 1) / kPlaneThreads;
+    float2 v[NI][B];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int it = tid + r * kPlaneThreads;
       const int a = it % A, q = it / A;
-      float2 v[B];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int n = a + A * b;
-        if constexpr (MODE == ROW_R2C) v[b] = make_float2(inr[(2 * q) * L2 + n], inr[(2 * q + 1) * L2 + n]);
-        else v[b] = P[q * L2 + n];
+        if (it >= PAIRS * A) v[r][b] = make_float2(0.f, 0.f);
+        else if constexpr (MODE == ROW_R2C)
+          v[r][b] = make_float2(inr[(2 * q) * L2 + n], inr[(2 * q + 1) * L2 + n]);
+        else v[r][b] = P[q * L2 + n];
       }
-      Dft<B, -1>::run(v);
+    }
 #pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a]);
+    for (int r = 0; r < NI; ++r) {
+      const int it = tid + r * kPlaneThreads;
+      if (it >= PAIRS * A) continue;
+      const int a = it % A, q = it / A;
+      Dft<B, -1>::run(v[r]);
 #pragma unroll
-      for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = v[kb];
+      for (int kb = 1; kb < B; ++kb) v[r][kb] = ctw<-1>(v[r][kb], tw[kb * A + a]);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = v[r][kb];
     }
     __syncthreads();
     for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
