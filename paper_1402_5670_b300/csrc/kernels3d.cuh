@@ -52,110 +52,56 @@ __device__ __forceinline__ void plane_col_fft(const float2* src, float2* wk, flo
   __syncthreads();
 }
 
-// Plane pass for slot blockIdx.y, plane blockIdx.x (axis-0 index i0).
+// Plane pass, persistent: work item i = (slot i / L0, plane i0 = i % L0); CTA c takes
+// items c, c + gridDim.x, ... (one plane in shared memory at a time).
 //   ROW_C2R  half-spectrum plane -> real plane * scale (optional threshold)
 //   ROW_R2C  real plane -> half-spectrum plane
 //   ROW_RT   half -> real * scale -> threshold -> half
+// The next item's input is loaded into registers while the current plane is
+// transformed (C2R: during the axis-1 FFT and the first row pass, then parked in the
+// plane buffer once that is free; R2C: during everything after the first row pass).
 // in/out slot strides are in elements of their own type. Spectra are tile-major
 // (p.tm): point p = k1 * NH + k2 of plane i0 lives at p.tm.at(i0, p); real planes are
 // row-major and plane i0 starts at i0 * (L1 * L2).
 template <int L1, int L2, int MODE>
-__global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
+__global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p, int nslots) {
   using G = PlaneGeom<L1, L2>;
   constexpr int NH = G::NH;
   constexpr int A = Split<L2>::A, B = Split<L2>::B;
   constexpr int LS = B * (A + 1);
   constexpr int PAIRS = L1 / 2;
   constexpr int H = L2 / 2;
+  constexpr int NIT = (G::HALF + kPlaneThreads - 1) / kPlaneThreads;  // gather loads
+  constexpr int NI = (PAIRS * A + kPlaneThreads - 1) / kPlaneThreads;  // row items
   extern __shared__ float2 sm[];
   float2* P = sm;
   float2* W = sm + G::S;
   const int tid = threadIdx.x;
-  const int slot = blockIdx.y, i0 = blockIdx.x;
+  const int L0 = p.n_rows;
+  const int nitems = nslots * L0;
   const float2* tw = g_twiddle + twiddle_offset(L2);
 
-  if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
+  // half-spectrum plane gather (C2R, RT) into registers
+  auto gather = [&](int item, float2 (&ld)[NIT]) {
+    const int slot = item / L0, i0 = item % L0;
     const float2* in = p.in_half + (int64_t)slot * p.in_stride;
-    // all of this thread's loads issued before any of them is used
-    constexpr int NIT = (G::HALF + kPlaneThreads - 1) / kPlaneThreads;
-    float2 ld[NIT];
 #pragma unroll
     for (int r = 0; r < NIT; ++r) {
       const int i = tid + r * kPlaneThreads;
       ld[r] = i < G::HALF ? in[p.tm.at(i0, i)] : make_float2(0.f, 0.f);
     }
+  };
+  auto park = [&](const float2 (&ld)[NIT]) {
 #pragma unroll
     for (int r = 0; r < NIT; ++r) {
       const int i = tid + r * kPlaneThreads;
       if (i < G::HALF) P[i] = ld[r];
     }
-    __syncthreads();
-    plane_col_fft<L1, NH, 1>(P, W, P);
-    // rows (2q, 2q+1): complex inverse DFT of the Hermitian-extended pair
-    for (int it = tid; it < PAIRS * A; it += kPlaneThreads) {
-      const int a = it % A, q = it / A;
-      const float2* r0 = P + (2 * q) * NH;
-      const float2* r1 = r0 + NH;
-      float2 v[B];
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const int n = a + A * b;
-        float2 ya, yb;
-        if (n <= H) {
-          ya = r0[n];
-          yb = r1[n];
-        } else {
-          ya = cconj(r0[L2 - n]);
-          yb = cconj(r1[L2 - n]);
-        }
-        v[b] = make_float2(ya.x - yb.y, ya.y + yb.x);
-      }
-      Dft<B, 1>::run(v);
-#pragma unroll
-      for (int kb = 1; kb < B; ++kb) v[kb] = ctw<1>(v[kb], tw[kb * A + a]);
-#pragma unroll
-      for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = v[kb];
-    }
-    __syncthreads();
-    const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
-    float* outr = nullptr;
-    if constexpr (MODE == ROW_C2R)
-      outr = p.out_real + (int64_t)slot * p.out_stride + (int64_t)i0 * (L1 * L2);
-    for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
-      const int kb = it % B, q = it / B;
-      float2 w[A];
-#pragma unroll
-      for (int a = 0; a < A; ++a) w[a] = W[q * LS + kb * (A + 1) + a];
-      Dft<A, 1>::run(w);
-#pragma unroll
-      for (int ka = 0; ka < A; ++ka) {
-        const int k = kb + B * ka;
-        float c0 = w[ka].x * p.scale, c1 = w[ka].y * p.scale;
-        if (p.use_thr) {
-          if (fabsf(c0) < thr) c0 = 0.f;
-          if (fabsf(c1) < thr) c1 = 0.f;
-        }
-        if constexpr (MODE == ROW_C2R) {
-          outr[(2 * q) * L2 + k] = c0;
-          outr[(2 * q + 1) * L2 + k] = c1;
-        } else {
-          P[q * L2 + k] = make_float2(c0, c1);  // natural pairs for the forward pass
-        }
-      }
-    }
-    if constexpr (MODE == ROW_C2R) return;
-    __syncthreads();
-  }
-
-  // real rows (pairs) -> half rows in W -> FFT along axis 1 -> out
-  {
-    const float* inr = nullptr;
-    if constexpr (MODE == ROW_R2C)
-      inr = p.in_real + (int64_t)slot * p.in_stride + (int64_t)i0 * (L1 * L2);
-    // this thread's items (a, q): all their input values are loaded before the first
-    // transform, so the global-memory latency is paid once
-    constexpr int NI = (PAIRS * A + kPlaneThreads - 1) / kPlaneThreads;
-    float2 v[NI][B];
+  };
+  // this thread's real row items (a, q) of a plane (R2C)
+  auto load_rows = [&](int item, float2 (&v)[NI][B]) {
+    const int slot = item / L0, i0 = item % L0;
+    const float* inr = p.in_real + (int64_t)slot * p.in_stride + (int64_t)i0 * (L1 * L2);
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       const int it = tid + r * kPlaneThreads;
@@ -163,12 +109,103 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int n = a + A * b;
-        if (it >= PAIRS * A) v[r][b] = make_float2(0.f, 0.f);
-        else if constexpr (MODE == ROW_R2C)
-          v[r][b] = make_float2(inr[(2 * q) * L2 + n], inr[(2 * q + 1) * L2 + n]);
-        else v[r][b] = P[q * L2 + n];
+        v[r][b] = it < PAIRS * A ? make_float2(inr[(2 * q) * L2 + n], inr[(2 * q + 1) * L2 + n])
+                                 : make_float2(0.f, 0.f);
       }
     }
+  };
+
+  int item = blockIdx.x;
+  float2 ld[MODE == ROW_R2C ? 1 : NIT];
+  float2 v[NI][B];
+  if (item < nitems) {
+    if constexpr (MODE == ROW_R2C) {
+      load_rows(item, v);
+    } else {
+      gather(item, ld);
+      park(ld);
+    }
+  }
+  for (; item < nitems; item += gridDim.x) {
+    const int slot = item / L0, i0 = item % L0;
+    const int next = item + gridDim.x;
+    if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
+      __syncthreads();  // the parked plane is in P
+      if constexpr (MODE == ROW_C2R) {
+        if (next < nitems) gather(next, ld);
+      }
+      plane_col_fft<L1, NH, 1>(P, W, P);
+      // rows (2q, 2q+1): complex inverse DFT of the Hermitian-extended pair
+      for (int it = tid; it < PAIRS * A; it += kPlaneThreads) {
+        const int a = it % A, q = it / A;
+        const float2* r0 = P + (2 * q) * NH;
+        const float2* r1 = r0 + NH;
+        float2 u[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const int n = a + A * b;
+          float2 ya, yb;
+          if (n <= H) {
+            ya = r0[n];
+            yb = r1[n];
+          } else {
+            ya = cconj(r0[L2 - n]);
+            yb = cconj(r1[L2 - n]);
+          }
+          u[b] = make_float2(ya.x - yb.y, ya.y + yb.x);
+        }
+        Dft<B, 1>::run(u);
+#pragma unroll
+        for (int kb = 1; kb < B; ++kb) u[kb] = ctw<1>(u[kb], tw[kb * A + a]);
+#pragma unroll
+        for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = u[kb];
+      }
+      __syncthreads();
+      if constexpr (MODE == ROW_C2R) {
+        if (next < nitems) park(ld);  // P is free: the rows are in W
+      }
+      const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
+      float* outr = nullptr;
+      if constexpr (MODE == ROW_C2R)
+        outr = p.out_real + (int64_t)slot * p.out_stride + (int64_t)i0 * (L1 * L2);
+      for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
+        const int kb = it % B, q = it / B;
+        float2 w[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) w[a] = W[q * LS + kb * (A + 1) + a];
+        Dft<A, 1>::run(w);
+#pragma unroll
+        for (int ka = 0; ka < A; ++ka) {
+          const int k = kb + B * ka;
+          float c0 = w[ka].x * p.scale, c1 = w[ka].y * p.scale;
+          if (p.use_thr) {
+            if (fabsf(c0) < thr) c0 = 0.f;
+            if (fabsf(c1) < thr) c1 = 0.f;
+          }
+          if constexpr (MODE == ROW_C2R) {
+            outr[(2 * q) * L2 + k] = c0;
+            outr[(2 * q + 1) * L2 + k] = c1;
+          } else {
+            P[q * L2 + k] = make_float2(c0, c1);  // natural pairs for the forward pass
+          }
+        }
+      }
+      if constexpr (MODE == ROW_C2R) continue;
+      __syncthreads();
+      // RT: this plane's rows, from P
+#pragma unroll
+      for (int r = 0; r < NI; ++r) {
+        const int it = tid + r * kPlaneThreads;
+        const int a = it % A, q = it / A;
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+          v[r][b] = it < PAIRS * A ? P[q * L2 + a + A * b] : make_float2(0.f, 0.f);
+      }
+    } else {
+      __syncthreads();  // the previous item is done with the shared buffers
+    }
+
+    // real rows (pairs) in v -> half rows in W -> FFT along axis 1 -> out
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       const int it = tid + r * kPlaneThreads;
@@ -179,6 +216,9 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
       for (int kb = 1; kb < B; ++kb) v[r][kb] = ctw<-1>(v[r][kb], tw[kb * A + a]);
 #pragma unroll
       for (int kb = 0; kb < B; ++kb) W[q * LS + kb * (A + 1) + a] = v[r][kb];
+    }
+    if constexpr (MODE == ROW_R2C) {
+      if (next < nitems) load_rows(next, v);  // v is free: in flight during the rest
     }
     __syncthreads();
     for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
@@ -202,6 +242,13 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p) {
     plane_col_fft<L1, NH, -1>(W, P, W);
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
     for (int i = tid; i < G::HALF; i += kPlaneThreads) out[p.tm.at(i0, i)] = W[i];
+    if constexpr (MODE == ROW_RT) {
+      __syncthreads();  // W read out before the next plane is parked in P... and W
+      if (next < nitems) {
+        gather(next, ld);
+        park(ld);
+      }
+    }
   }
 }
 

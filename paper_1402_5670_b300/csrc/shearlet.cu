@@ -398,8 +398,12 @@ static cudaError_t launch_plane_t(dim3 grid, cudaStream_t st, const RowArgs& a) 
   constexpr int smem = sl::dev::PlaneGeom<L1, L2>::bytes;
   cudaError_t e = ensure_smem(k, smem);
   if (e != cudaSuccess) return e;
+  // persistent: grid.x planes x grid.y slots of work, as many CTAs as fit
+  const int nslots = (int)grid.y, items = (int)grid.x * nslots;
+  const int g = std::min(items, persistent_grid(k, kPlaneThreads, smem, 7000 + 1000 * MODE + 10 * L1 + L2 / 8));
   static const char* names[3] = {"plane_r2c", "plane_c2r", "plane_roundtrip"};
-  return timed_launch(names[MODE], st, [&]() { k<<<grid, kPlaneThreads, smem, st>>>(a); });
+  return timed_launch(names[MODE], st,
+                      [&]() { k<<<g, kPlaneThreads, smem, st>>>(a, nslots); });
 }
 
 template <int L1, int MODE>
