@@ -809,15 +809,23 @@ __global__ void __launch_bounds__(256) k_threshold(float* c, int64_t n, int nf, 
   float* base = c + (int64_t)f * n;
   const int64_t n4 = n / 4;
   float4* b4 = reinterpret_cast<float4*>(base);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float4 v = b4[i];
+  auto thr4 = [t](float4 v) {
     v.x = fabsf(v.x) < t ? 0.f : v.x;
     v.y = fabsf(v.y) < t ? 0.f : v.y;
     v.z = fabsf(v.z) < t ? 0.f : v.z;
     v.w = fabsf(v.w) < t ? 0.f : v.w;
-    b4[i] = v;
+    return v;
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n4; i += 4 * stride) {  // four loads in flight per thread
+    const float4 v0 = b4[i], v1 = b4[i + stride], v2 = b4[i + 2 * stride], v3 = b4[i + 3 * stride];
+    b4[i] = thr4(v0);
+    b4[i + stride] = thr4(v1);
+    b4[i + 2 * stride] = thr4(v2);
+    b4[i + 3 * stride] = thr4(v3);
   }
+  for (; i < n4; i += stride) b4[i] = thr4(b4[i]);
   for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     base[i] = fabsf(base[i]) < t ? 0.f : base[i];
