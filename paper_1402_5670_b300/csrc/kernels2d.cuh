@@ -549,16 +549,29 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
     float2 res[A];
     if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
       const float2* in = reinterpret_cast<const float2*>(stg + stage * stage_bytes);
+      const float2* in0 = in + (2 * line1) * NPp;
+      const float2* in1 = in0 + NPp;
       float2 v[B];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
+        // n = a1 + A b with 0 <= a1 < A: below H for (b + 1) A <= H, above H for
+        // b A > H (both known once the loop is unrolled); only one b straddles H
         const int n = a1 + A * b;
-        const int m = n <= H ? n : L - n;
-        float2 ya = in[(2 * line1) * NPp + m];
-        float2 yb = in[(2 * line1 + 1) * NPp + m];
-        if (n > H) {
-          ya = cconj(ya);
-          yb = cconj(yb);
+        float2 ya, yb;
+        if ((b + 1) * A <= H) {
+          ya = in0[n];
+          yb = in1[n];
+        } else if (b * A > H) {
+          ya = cconj(in0[L - n]);
+          yb = cconj(in1[L - n]);
+        } else {
+          const int m = n <= H ? n : L - n;
+          ya = in0[m];
+          yb = in1[m];
+          if (n > H) {
+            ya = cconj(ya);
+            yb = cconj(yb);
+          }
         }
         v[b] = make_float2(ya.x - yb.y, ya.y + yb.x);
       }
@@ -641,13 +654,19 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
     }
     __syncthreads();
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
-    constexpr int HP = H + 1;
-    for (int it = tid; it < PAIRS * HP; it += T) {
-      const int line = it / HP, kk = it % HP;
-      const float2 z = sm[line * L + kk];
-      const float2 w = sm[line * L + (kk == 0 ? 0 : L - kk)];
-      out[tm.at(r0 + 2 * line, kk)] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
-      out[tm.at(r0 + 2 * line + 1, kk)] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+    // lines outer, points inner (no divisions); the two rows of a pair sit TC elements
+    // apart in the tile-major layout
+    const int tcs = tm_tc(tm);
+#pragma unroll
+    for (int line = 0; line < PAIRS; ++line) {
+      const float2* zl = sm + line * L;
+      for (int kk = tid; kk <= H; kk += T) {
+        const float2 z = zl[kk];
+        const float2 w = zl[kk == 0 ? 0 : L - kk];
+        float2* o = out + tm.at(r0 + 2 * line, kk);
+        o[0] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
+        o[tcs] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+      }
     }
     __syncthreads();  // exchange reused by the next item
   }
