@@ -282,6 +282,7 @@ def test_adjoint_identity(case):
 
 
 @pytest.mark.parametrize("case", [((16, 16), 2, (0, 1)), ((16, 16), 1, (1,)),
+                                  ((24, 16), 1, (1,)), ((12, 24), 1, (0,)),
                                   ((8, 8, 8), 1, (0,)), ((8, 8, 8), 1, (1,))], ids=str)
 def test_forward_equals_bruteforce_correlation(case):
     """eq. convolution: C_j(m) = (x * conj(psi_j))(m) = sum_n x(n) psi_j(n - m), summed
