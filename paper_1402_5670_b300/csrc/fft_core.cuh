@@ -1,7 +1,8 @@
 // Register-resident small DFTs and the two-pass line-FFT decomposition used by every
 // transform kernel of libshearlet. Internal header.
 //
-// A length-L line is split as L = A * B (both powers of two). With n = a + A b and
+// A length-L line is split as L = A * B (powers of two, or 384 = 24 * 16). With
+// n = a + A b and
 // k = kb + B ka,
 //   X[kb + B ka] = sum_a W_A^{a ka} * ( W_L^{a kb} * sum_b x[a + A b] W_B^{b kb} ).
 // Pass 1 gives each thread the B samples x[a + A b] of one (line, a): a DFT of length

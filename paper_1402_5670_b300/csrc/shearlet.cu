@@ -347,7 +347,8 @@ static cudaError_t launch_col_tc(int L, bool fwd, int nitems, cudaStream_t st, c
 
 // Row passes: PAIRS row pairs per CTA. Launches over many filters use the wide
 // variant (col_tile_of(L) pairs); single-image launches use one pair per CTA so that
-// the few rows of one image still spread over many SMs.
+// the few rows of one image still spread over many SMs (rows of 512 and 1024 points:
+// the one-warp kernel k_row_warp).
 template <int L, int MODE, int PAIRS>
 static cudaError_t launch_row_p(dim3 grid, cudaStream_t st, const RowArgs& a) {
   auto k = sl::dev::k_row<L, MODE, PAIRS>;
@@ -573,7 +574,7 @@ static void free_device(sl_bank* b) {
 
 // Grouping: the per-filter intermediate spectra of one group stay resident in L2
 // between the two passes of a transform; a group holds as many filters as fit in
-// the scratch budget (SL_SCRATCH_MB, default 48 MB).
+// the scratch budget (environment variable SL_SCRATCH_MB, default 256 MB).
 static void plan_groups(sl_bank* b) {
   // Default budget for the per-filter intermediates: 256 MB holds all 49 spectra of
   // a 1024^2 four-scale system, so the filter loop runs as one group (fewer, larger
