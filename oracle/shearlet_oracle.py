@@ -706,6 +706,38 @@ def denoise(x: np.ndarray, sysm: ShearletSystem, sigma: float, K: Sequence[float
     return np.real(np.fft.ifftn(acc))
 
 
+def inpaint_ratio(delta_init: float, delta_min: float, iterations: int) -> float:
+    """The factor lambda of the threshold schedule delta_{k+1} = lambda delta_k of the
+    inpainting algorithm (Sec. 5.4). Reading: the paper writes lambda = delta_min^(1 /
+    (iterations - 1)), i.e. delta_min relative to delta_init; here lambda is chosen so
+    that the last iteration thresholds at delta_min itself:
+    delta_init lambda^(iterations - 1) = delta_min."""
+    if iterations <= 1:
+        return 1.0
+    return (float(delta_min) / float(delta_init)) ** (1.0 / (iterations - 1))
+
+
+def inpaint(f_masked: np.ndarray, mask: np.ndarray, sysm: ShearletSystem, delta_init: float,
+            delta_min: float, iterations: int, dtype=np.float64) -> np.ndarray:
+    """Image inpainting by iterative thresholding (Sec. 5.4, algorithm
+    image_inpainting): starting from 0, each iteration adds the residual on the known
+    pixels, f_res = M (f_masked - f_inpainted), and replaces f_inpainted by
+    T^-1 T_delta T (f_res + f_inpainted); delta then shrinks by inpaint_ratio.
+    Reading: T_delta thresholds subband j >= 1 at delta ||psi_j||_2 (the denoising
+    convention with K = 1 and sigma = delta) and keeps the lowpass."""
+    M = (np.asarray(mask) != 0).astype(np.float64)
+    f = np.asarray(f_masked, dtype=np.float64)
+    out = np.zeros_like(f)
+    lam = inpaint_ratio(delta_init, delta_min, iterations)
+    ones = [1.0] * sysm.n_scales
+    delta = float(delta_init)
+    for _ in range(int(iterations)):
+        res = M * (f - out)
+        out = denoise(res + out, sysm, delta, ones, dtype)
+        delta *= lam
+    return out
+
+
 def psnr(f: np.ndarray, g: np.ndarray, peak: float = 255.0) -> float:
     """PSNR = 20 log10( peak sqrt(N) / ||f - g||_F )  (eq. PSNR)."""
     f = np.asarray(f, dtype=np.float64)

@@ -100,6 +100,24 @@ def gaussian_field(shape: Sequence[int], seed: int, scale: float = 1.0) -> np.nd
     return (float(scale) * _rng(seed).standard_normal(tuple(shape))).astype(np.float32)
 
 
+def random_mask(shape: Sequence[int], missing: float, seed: int) -> np.ndarray:
+    """Binary mask (uint8, 1 = known pixel) with a fraction ``missing`` of the pixels
+    occluded at random (the paper's "Random" mask occludes 80%)."""
+    return (_rng(seed).random(tuple(shape)) >= float(missing)).astype(np.uint8)
+
+
+def squares_mask(shape: Sequence[int], n_squares: int, side: int, seed: int) -> np.ndarray:
+    """Binary mask (uint8, 1 = known pixel) with ``n_squares`` occluded squares of
+    ``side`` pixels at random positions (the paper's "Squares" mask)."""
+    r = _rng(seed)
+    m = np.ones(tuple(shape), dtype=np.uint8)
+    for _ in range(int(n_squares)):
+        y = int(r.integers(0, max(1, shape[0] - side)))
+        x = int(r.integers(0, max(1, shape[1] - side)))
+        m[y:y + side, x:x + side] = 0
+    return m
+
+
 def uneven_batch_shapes(n: int, sides: Sequence[int], seed: int) -> List[Tuple[int, int]]:
     """n image shapes (n0, n1) with each side drawn independently from ``sides``."""
     r = _rng(seed)

@@ -415,3 +415,60 @@ def test_pin_catches_swapped_wavelet_axes(monkeypatch):
     assert frac_in_cone1() > 0.9
     monkeypatch.setattr(O, "_unsheared_2d", bad_unsheared)
     assert frac_in_cone1() < 0.5
+
+
+# ------------------------------------------------------------------ inpainting ---
+
+def test_inpaint_schedule_ends_at_delta_min():
+    """Sec. 5.4: delta shrinks geometrically from delta_init to delta_min."""
+    lam = O.inpaint_ratio(50.0, 2.0, 11)
+    assert abs(50.0 * lam ** 10 - 2.0) < 1e-12
+    assert O.inpaint_ratio(5.0, 1.0, 1) == 1.0
+
+
+def test_inpaint_without_occlusion_is_perfect_reconstruction():
+    """Mask of ones and a threshold far below every coefficient: one iteration is
+    T^-1 T f = f (eq. reconstruction)."""
+    dims = (32, 32)
+    s = oracle_system(dims, 2, (1, 1))
+    f = synth.piecewise_smooth_image(dims, 3).astype(np.float64)
+    out = O.inpaint(f, np.ones(dims, np.uint8), s, 1e-12, 1e-12, 1)
+    assert np.max(np.abs(out - f)) <= 1e-10 * np.max(np.abs(f))
+
+
+def test_inpaint_without_thresholding_keeps_the_known_pixels_only():
+    """With no coefficient thresholded the iteration is f_k+1 = M f_masked + (1 - M) f_k
+    (M^2 = M), whose fixed point reached at once from 0 is M f_masked: the unknown
+    pixels stay 0. A sign slip in the residual breaks this."""
+    dims = (32, 32)
+    s = oracle_system(dims, 2, (1, 1))
+    f = synth.piecewise_smooth_image(dims, 4).astype(np.float64)
+    M = synth.random_mask(dims, 0.5, 5)
+    out = O.inpaint(f * M, M, s, 1e-12, 1e-12, 3)
+    assert np.max(np.abs(out - f * M)) <= 1e-9 * np.max(np.abs(f))
+
+
+def test_inpainting_fills_the_holes():
+    """Iterative thresholding recovers most of a randomly 60%-occluded cartoon image:
+    far better PSNR than the masked image, and better than the mean fill."""
+    dims = (64, 64)
+    s = oracle_system(dims, 3, (0, 1, 1))
+    f = synth.piecewise_smooth_image(dims, 6).astype(np.float64)
+    M = synth.random_mask(dims, 0.6, 7)
+    out = O.inpaint(f * M, M, s, 200.0, 2.0, 30)
+    mean_fill = np.where(M > 0, f, np.mean(f[M > 0]))
+    assert O.psnr(f, out) > O.psnr(f, mean_fill) + 3.0
+    assert O.psnr(f, out) > O.psnr(f, f * M) + 10.0
+
+
+def test_pin_catches_residual_sign_slip():
+    """Planted mistake (a copy of the iteration with f_res = M (f_inpainted - f_masked)):
+    the fixed-point pin above must fail for it."""
+    dims = (32, 32)
+    s = oracle_system(dims, 2, (1, 1))
+    f = synth.piecewise_smooth_image(dims, 4).astype(np.float64)
+    M = synth.random_mask(dims, 0.5, 5).astype(np.float64)
+    out = np.zeros_like(f)
+    for _ in range(3):
+        out = O.denoise(M * (out - f * M) + out, s, 1e-12, [1.0, 1.0])
+    assert np.max(np.abs(out - f * M)) > 1e-3 * np.max(np.abs(f))
