@@ -184,6 +184,21 @@ sl_status sl_denoise(const sl_bank* bank, const float* noisy, float* out, float 
                      const float* K, void* stream);
 
 /*
+ * Image inpainting by iterative thresholding (Sec. 5.4, algorithm image_inpainting).
+ * f_masked: DEVICE [dims] image with the occluded pixels set to anything; mask: DEVICE
+ * uint8 [dims], nonzero = known pixel; out: DEVICE [dims] result (must not alias
+ * f_masked). Starting from 0, each of the `iterations` steps sets the known pixels
+ * of the current estimate to f_masked and replaces the estimate by the fused
+ * denoising of it (as sl_denoise with K = 1 for every scale and sigma = delta, i.e.
+ * subband j >= 1 thresholded at delta ||psi_j||_2, the lowpass kept); delta starts
+ * at delta_init and shrinks geometrically to delta_min at the last step. The bank
+ * keeps one [dims] float buffer for the iterate (allocated on first use). Work per
+ * step: one elementwise pass and one fused denoise.
+ */
+sl_status sl_inpaint(const sl_bank* bank, const float* f_masked, const uint8_t* mask, float* out,
+                     float delta_init, float delta_min, int iterations, void* stream);
+
+/*
  * End-to-end round trip from HOST memory: copies x_host[dims] to the device,
  * runs sl_forward into library-owned coefficient memory, then sl_inverse, and
  * copies the reconstruction back to y_host[dims]. Host arrays should be pinned

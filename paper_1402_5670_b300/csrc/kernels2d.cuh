@@ -850,5 +850,30 @@ __global__ void __launch_bounds__(256) k_threshold(float* c, int64_t n, int nf, 
     base[i] = fabsf(base[i]) < t ? 0.f : base[i];
 }
 
+// Inpainting step input: u = f + M (f_masked - f) with M = (mask != 0); f = 0 when
+// f_cur is null (the first iteration). Four elements per thread and step.
+__global__ void __launch_bounds__(256) k_inpaint_mix(const float* __restrict__ fm,
+                                                     const uint8_t* __restrict__ mask,
+                                                     const float* __restrict__ f_cur,
+                                                     float* __restrict__ u, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < n; i += stride) {
+    const int64_t e = 4 * i;
+    if (e + 3 < n) {
+      const float4 a = reinterpret_cast<const float4*>(fm)[i];
+      const uchar4 m = reinterpret_cast<const uchar4*>(mask)[i];
+      float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (f_cur) f = reinterpret_cast<const float4*>(f_cur)[i];
+      reinterpret_cast<float4*>(u)[i] =
+          make_float4(m.x ? a.x : f.x, m.y ? a.y : f.y, m.z ? a.z : f.z, m.w ? a.w : f.w);
+    } else {
+      for (int64_t k = e; k < n; ++k) {
+        const float f = f_cur ? f_cur[k] : 0.f;
+        u[k] = mask[k] ? fm[k] : f;
+      }
+    }
+  }
+}
+
 }  // namespace dev
 }  // namespace sl

@@ -537,6 +537,7 @@ struct sl_bank {
   double* invPsi_cl = nullptr;
   float2* xhat_cl = nullptr;  // [TOTAL]
   float2* part_cl = nullptr;  // [ncl][TOTAL]
+  float* inp_u = nullptr;     // sl_inpaint's iterate input (allocated on first use)
   float* e2e_x = nullptr;     // sl_fwdinv_host buffers (allocated on first use)
   float* e2e_c = nullptr;
   cudaStream_t e2e_cap = nullptr;         // sl_fwdinv_host: capture stream, graph and the
@@ -555,6 +556,8 @@ static void free_device(sl_bank* b) {
   cudaFree(b->partial);
   cudaFree(b->e2e_x);
   cudaFree(b->e2e_c);
+  cudaFree(b->inp_u);
+  b->inp_u = nullptr;
   if (b->e2e_graph) cudaGraphExecDestroy(b->e2e_graph);
   if (b->e2e_cap) cudaStreamDestroy(b->e2e_cap);
   b->e2e_graph = nullptr;
@@ -1270,6 +1273,45 @@ sl_status sl_denoise(const sl_bank* b, const float* noisy, float* out, float sig
   SL_TRY(check_aligned(noisy, out));
   if (!(sigma >= 0.f) || !std::isfinite(sigma)) return fail(SL_EINVAL, "sigma must be >= 0");
   return denoise_plan(plan_of(b), noisy, out, sigma, K, (cudaStream_t)stream);
+}
+
+sl_status sl_inpaint(const sl_bank* cb, const float* f_masked, const uint8_t* mask, float* out,
+                     float delta_init, float delta_min, int iterations, void* stream) {
+  SL_TRY(check_call(cb));
+  if (!f_masked || !mask || !out) return fail(SL_EINVAL, "f_masked, mask or out is NULL");
+  SL_TRY(check_aligned(f_masked, out));
+  if (!a16(mask)) return fail(SL_EINVAL, "device arrays must be 16-byte aligned");
+  if (iterations < 1) return fail(SL_EINVAL, "iterations must be >= 1");
+  if (!(delta_init > 0.f) || !(delta_min > 0.f) || !std::isfinite(delta_init) ||
+      !std::isfinite(delta_min))
+    return fail(SL_EINVAL, "delta_init and delta_min must be finite and > 0");
+  sl_bank* b = const_cast<sl_bank*>(cb);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!b->inp_u && cudaMalloc((void**)&b->inp_u, (size_t)b->N * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    b->inp_u = nullptr;
+    return fail(SL_ENOMEM, "allocating the inpainting buffer");
+  }
+  // delta_k = delta_init lambda^k with delta_init lambda^(iterations - 1) = delta_min
+  const double lam = iterations > 1 ? std::pow((double)delta_min / (double)delta_init,
+                                               1.0 / (double)(iterations - 1))
+                                    : 1.0;
+  std::vector<float> ones((size_t)b->spec.J, 1.0f);
+  const Plan P = plan_of(b);
+  const int64_t n = b->N;
+  const int grid = (int)std::min<int64_t>((n / 4 + 255) / 256, 4 * 148);
+  double delta = delta_init;
+  for (int it = 0; it < iterations; ++it) {
+    const float* fcur = it == 0 ? nullptr : out;
+    float* u = b->inp_u;
+    SL_TRY(launched(timed_launch("inpaint_mix", st, [&]() {
+                      sl::dev::k_inpaint_mix<<<grid, 256, 0, st>>>(f_masked, mask, fcur, u, n);
+                    }),
+                    "inpaint_mix"));
+    SL_TRY(denoise_plan(P, u, out, (float)delta, ones.data(), st));
+    delta *= lam;
+  }
+  return SL_OK;
 }
 
 sl_status sl_fwdinv_host(const sl_bank* cb, const float* x_host, float* y_host, void* stream) {

@@ -52,6 +52,8 @@ SIGNATURES = {
     "sl_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _c_float_p, _vp]),
     "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sl_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sl_inpaint": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                  _vp]),
     "sl_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "sl_batch_free": (None, [_vp]),
     "sl_batch_info": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
@@ -343,6 +345,19 @@ class Bank:
         out = self._empty(self.dims) if out is None else out
         sl_denoise(self.handle, _dev_ptr(noisy, "noisy", self.N), _dev_ptr(out, "out", self.N),
                    sigma, K, _stream_ptr(stream))
+        return out
+
+    def inpaint(self, f_masked, mask, delta_init: float, delta_min: float, iterations: int,
+                out=None, stream=None):
+        """Iterative-thresholding inpainting (sl_inpaint); mask: uint8 CUDA tensor."""
+        import torch
+        if not (isinstance(mask, torch.Tensor) and mask.is_cuda and mask.dtype == torch.uint8
+                and mask.is_contiguous() and mask.numel() == self.N):
+            raise TypeError("mask must be a contiguous uint8 CUDA tensor of the image size")
+        out = self._empty(self.dims) if out is None else out
+        _check(lib().sl_inpaint(self.handle, _dev_ptr(f_masked, "f_masked", self.N), mask.data_ptr(),
+                                _dev_ptr(out, "out", self.N), float(delta_init), float(delta_min),
+                                int(iterations), _stream_ptr(stream)), "sl_inpaint")
         return out
 
     def fwdinv_host(self, x_host, y_host, stream=None):
