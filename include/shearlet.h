@@ -116,6 +116,33 @@ sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales,
                               const int* shearLevels, int fullSystem, int device,
                               const sl_options* opt, sl_bank** out);
 
+/* User-supplied filters of the construction (Sec. 4.1: the quadrature mirror
+ * filter's lowpass, h_1 of eq. lowhigh, and the 2D directional filter, P of eq.
+ * nonsep). NULL pointers keep the built-in designs (the symmetric maximally flat
+ * 9-tap lowpass of Sec. 5.1 and a maximally flat fan filter).
+ *   qmf:  qmf_len taps h(-m..m) (qmf_len = 2m + 1), symmetric: h(-n) = h(n);
+ *         the highpass is g(n) = (-1)^n h(n).
+ *   fan:  fan_rows x fan_cols taps P(n1, n2), row-major, centred (both sizes odd),
+ *         point-symmetric: P(-n) = P(n); rows pair with xi_1 (the principal axis of
+ *         the first cone), columns with xi_2.
+ * Symmetry (to 1e-12 relative) keeps every filter's spectrum real and even, which
+ * the transforms rely on; asymmetric taps, even sizes, more than 129 qmf taps or
+ * more than 65 x 65 fan taps are SL_EINVAL, and so is a system whose frame weight
+ * Psi vanishes somewhere on the grid. Taps are copied. */
+typedef struct {
+  const double* qmf;
+  int qmf_len;
+  const double* fan;
+  int fan_rows;
+  int fan_cols;
+} sl_filters;
+
+/* sl_build_filters_ex with user filters (filters may be NULL: built-in designs). */
+sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales,
+                                const int* shearLevels, int fullSystem, int device,
+                                const sl_options* opt, const sl_filters* filters,
+                                sl_bank** out);
+
 /* Release a bank and all library memory it holds. NULL is ignored. Call it with no
  * transform of this bank still running on the GPU. */
 void sl_free_filters(sl_bank* bank);

@@ -30,6 +30,7 @@
 #include <atomic>
 #include <cmath>
 #include <thread>
+#include <string>
 
 namespace sl {
 
@@ -75,38 +76,113 @@ inline double pow2(int e) { return std::ldexp(1.0, e); }
 
 }  // namespace
 
-double resp_lowpass(double w) { return H_of_s(0.5 * (1.0 - std::cos(w))); }
+// DTFT of symmetric taps h(-m..m): h(0) + 2 sum_{n>0} h(n) cos(n w) (real).
+static double user_lowpass(const std::vector<double>& h, double w) {
+  const int m = ((int)h.size() - 1) / 2;
+  const double c1 = std::cos(w);
+  double acc = h[m], cp = 1.0, cn = c1;  // cos((n-1) w), cos(n w) by recurrence
+  for (int n = 1; n <= m; ++n) {
+    acc += 2.0 * h[m + n] * cn;
+    const double nx = 2.0 * c1 * cn - cp;
+    cp = cn;
+    cn = nx;
+  }
+  return acc;
+}
 
-double resp_lowpass_j(int j, double w) {
+// DTFT of point-symmetric 2D taps: sum p(n1, n2) cos(n1 w1 + n2 w2) (real).
+static double user_fan(const FilterDesign& D, double w1, double w2) {
+  const int m1 = (D.pr - 1) / 2, m2 = (D.pc - 1) / 2;
+  double c1[65], s1[65], c2[65], s2[65];  // cos, sin of n w for n = 0..m
+  c1[0] = 1.0, s1[0] = 0.0, c2[0] = 1.0, s2[0] = 0.0;
+  const double a = std::cos(w1), b = std::sin(w1), c = std::cos(w2), e = std::sin(w2);
+  for (int n = 1; n <= m1; ++n) {
+    c1[n] = c1[n - 1] * a - s1[n - 1] * b;
+    s1[n] = s1[n - 1] * a + c1[n - 1] * b;
+  }
+  for (int n = 1; n <= m2; ++n) {
+    c2[n] = c2[n - 1] * c - s2[n - 1] * e;
+    s2[n] = s2[n - 1] * c + c2[n - 1] * e;
+  }
+  double acc = 0.0;
+  for (int i = 0; i < D.pr; ++i) {
+    const int n1 = i - m1;
+    const double ca = c1[n1 < 0 ? -n1 : n1], sa = n1 < 0 ? -s1[-n1] : s1[n1];
+    const double* row = D.p.data() + (size_t)i * D.pc;
+    for (int k = 0; k < D.pc; ++k) {
+      const int n2 = k - m2;
+      const double cb = c2[n2 < 0 ? -n2 : n2], sb = n2 < 0 ? -s2[-n2] : s2[n2];
+      acc += row[k] * (ca * cb - sa * sb);
+    }
+  }
+  return acc;
+}
+
+double resp_lowpass(const FilterDesign* D, double w) {
+  if (D && !D->h.empty()) return user_lowpass(D->h, w);
+  return H_of_s(0.5 * (1.0 - std::cos(w)));
+}
+
+double resp_lowpass_j(const FilterDesign* D, int j, double w) {
   double p = 1.0;
-  for (int i = 0; i < j; ++i) p *= resp_lowpass(pow2(i) * w);
+  for (int i = 0; i < j; ++i) p *= resp_lowpass(D, pow2(i) * w);
   return p;
 }
 
-static double resp_highpass(double w) { return H_of_s(0.5 * (1.0 + std::cos(w))); }
-
-double resp_highpass_j(int j, double w) {
-  return resp_highpass(pow2(j - 1) * w) * resp_lowpass_j(j - 1, w);
+// G(w) = H(w + pi): g(n) = (-1)^n h(n)
+static double resp_highpass(const FilterDesign* D, double w) {
+  if (D && !D->h.empty()) return user_lowpass(D->h, w + kPi);
+  return H_of_s(0.5 * (1.0 + std::cos(w)));
 }
 
-double resp_fan(double w1, double w2) {
+double resp_highpass_j(const FilterDesign* D, int j, double w) {
+  return resp_highpass(D, pow2(j - 1) * w) * resp_lowpass_j(D, j - 1, w);
+}
+
+double resp_fan(const FilterDesign* D, double w1, double w2) {
+  if (D && !D->p.empty()) return user_fan(*D, w1, w2);
   const FanDesign& f = fan();
   const double t = 0.5 * (std::cos(w2) - std::cos(w1));
   const double t2 = t * t;
   return 0.5 + t * (f.c[0] + t2 * (f.c[1] + t2 * (f.c[2] + t2 * f.c[3])));
 }
 
+std::string check_design(const FilterDesign& d) {
+  if (!d.h.empty()) {
+    const int n = (int)d.h.size();
+    if (n % 2 == 0 || n > 129) return "qmf taps: odd length up to 129 required";
+    double mx = 0.0;
+    for (double v : d.h) mx = std::max(mx, std::fabs(v));
+    if (!(mx > 0.0) || !std::isfinite(mx)) return "qmf taps must be finite and not all zero";
+    for (int i = 0; i < n; ++i)
+      if (std::fabs(d.h[i] - d.h[n - 1 - i]) > 1e-12 * mx)
+        return "qmf taps must be symmetric (h(-n) = h(n)), so that the spectra are real";
+  }
+  if (!d.p.empty()) {
+    if (d.pr % 2 == 0 || d.pc % 2 == 0 || d.pr > 65 || d.pc > 65 ||
+        (size_t)d.pr * d.pc != d.p.size())
+      return "fan taps: odd sizes up to 65 x 65 required";
+    double mx = 0.0;
+    for (double v : d.p) mx = std::max(mx, std::fabs(v));
+    if (!(mx > 0.0) || !std::isfinite(mx)) return "fan taps must be finite and not all zero";
+    for (size_t i = 0; i < d.p.size(); ++i)
+      if (std::fabs(d.p[i] - d.p[d.p.size() - 1 - i]) > 1e-12 * mx)
+        return "fan taps must be point-symmetric (P(-n) = P(n)), so that the spectra are real";
+  }
+  return "";
+}
+
 // Phi_{j,k}(a, b) for scale j with shear level d, J scales.
-static double phi_resp(int J, int j, int d, int k, double a, double b) {
+static double phi_resp(const FilterDesign* D, int J, int j, int d, int k, double a, double b) {
   const int m = J - j + d;
   const double pa = pow2(J - j - 1) * a;
   const int nr = 1 << d;
   double acc = 0.0;
   for (int r = 0; r < nr; ++r) {
     const double o = (a + 2.0 * kPi * r) / nr;
-    const double wd = resp_lowpass_j(d, o);
+    const double wd = resp_lowpass_j(D, d, o);
     const double eta = b - k * o;
-    acc += wd * wd * resp_lowpass_j(m, eta) * resp_fan(pa, pow2(m) * eta);
+    acc += wd * wd * resp_lowpass_j(D, m, eta) * resp_fan(D, pa, pow2(m) * eta);
   }
   return acc;
 }
@@ -150,6 +226,7 @@ int BankEvaluator::phi_index(int scale, int k, int pa, int pb) const {
 
 void BankEvaluator::build_3d_tables() {
   const BankSpec& s = spec_;
+  const FilterDesign* D = s.design.get();
   g1_.assign(s.J * 3, {});
   phi2_.assign(s.J * (2 * kmax_ + 1) * 9, {});
   for (int j = 0; j < s.J; ++j) {
@@ -157,7 +234,7 @@ void BankEvaluator::build_3d_tables() {
       std::vector<double>& t = g1_[j * 3 + ax];
       t.resize(s.dims[ax]);
       for (int64_t i = 0; i < s.dims[ax]; ++i)
-        t[i] = resp_highpass_j(s.J - j, 2.0 * kPi * i / s.dims[ax]);
+        t[i] = resp_highpass_j(D, s.J - j, 2.0 * kPi * i / s.dims[ax]);
     }
     const int e = 1 << s.d[j];
     for (int pyr = 1; pyr <= 3; ++pyr) {
@@ -171,7 +248,7 @@ void BankEvaluator::build_3d_tables() {
           t.resize(np * nq);
           for (int64_t ip = 0; ip < np; ++ip)
             for (int64_t iq = 0; iq < nq; ++iq)
-              t[ip * nq + iq] = phi_resp(s.J, j, s.d[j], k, 2.0 * kPi * ip / np,
+              t[ip * nq + iq] = phi_resp(D, s.J, j, s.d[j], k, 2.0 * kPi * ip / np,
                                          2.0 * kPi * iq / nq);
         }
       }
@@ -181,12 +258,13 @@ void BankEvaluator::build_3d_tables() {
 
 void BankEvaluator::eval_2d(const FilterDesc& f, double* out) const {
   const BankSpec& s = spec_;
+  const FilterDesign* D = s.design.get();
   const int64_t n0 = s.dims[0], n1 = s.dims[1], nh = s.nh();
   if (f.scale < 0) {
     for (int64_t i0 = 0; i0 < n0; ++i0) {
-      const double a = resp_lowpass_j(s.J, 2.0 * kPi * i0 / n0);
+      const double a = resp_lowpass_j(D, s.J, 2.0 * kPi * i0 / n0);
       for (int64_t i1 = 0; i1 < nh; ++i1)
-        out[i0 * nh + i1] = a * resp_lowpass_j(s.J, 2.0 * kPi * i1 / n1);
+        out[i0 * nh + i1] = a * resp_lowpass_j(D, s.J, 2.0 * kPi * i1 / n1);
     }
     return;
   }
@@ -197,20 +275,21 @@ void BankEvaluator::eval_2d(const FilterDesc& f, double* out) const {
       const double x1 = 2.0 * kPi * i1 / n1;
       const double a = f.cone == 1 ? x0 : x1;  // principal axis
       const double b = f.cone == 1 ? x1 : x0;
-      out[i0 * nh + i1] = resp_highpass_j(s.J - j, a) * phi_resp(s.J, j, d, f.k1, a, b);
+      out[i0 * nh + i1] = resp_highpass_j(D, s.J - j, a) * phi_resp(D, s.J, j, d, f.k1, a, b);
     }
   }
 }
 
 void BankEvaluator::eval_3d(const FilterDesc& f, double* out) const {
   const BankSpec& s = spec_;
+  const FilterDesign* D = s.design.get();
   const int64_t n0 = s.dims[0], n1 = s.dims[1], n2 = s.dims[2], nh = s.nh();
   if (f.scale < 0) {
     std::vector<double> l[3];
     for (int ax = 0; ax < 3; ++ax) {
       l[ax].resize(s.dims[ax]);
       for (int64_t i = 0; i < s.dims[ax]; ++i)
-        l[ax][i] = resp_lowpass_j(s.J, 2.0 * kPi * i / s.dims[ax]);
+        l[ax][i] = resp_lowpass_j(D, s.J, 2.0 * kPi * i / s.dims[ax]);
     }
     for (int64_t i0 = 0; i0 < n0; ++i0)
       for (int64_t i1 = 0; i1 < n1; ++i1)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -15,7 +16,16 @@ struct FilterDesc {
   int k2;     // second shear (3D), 0 in 2D
 };
 
+// User-supplied filters (Sec. 4.1: the QMF lowpass and the 2D fan filter are inputs of
+// the construction). Empty vectors select the built-in designs.
+struct FilterDesign {
+  std::vector<double> h;  // taps h(-m..m), odd length, symmetric
+  std::vector<double> p;  // taps P(n1, n2), [pr][pc] row-major, centred, point-symmetric
+  int pr = 0, pc = 0;     // (axis 0 of P pairs with xi_1, axis 1 with xi_2)
+};
+
 struct BankSpec {
+  std::shared_ptr<const FilterDesign> design;  // null: built-in filters
   int ndim = 2;
   int64_t dims[3] = {1, 1, 1};
   int J = 1;
@@ -69,10 +79,14 @@ struct HostBank {
 // want_psi32 = false skips the FP32 bank (host-only banks).
 bool build_host_bank(const BankSpec& s, bool want_psi32, HostBank* out, std::string* err);
 
-// Closed-form 1D/2D responses (exposed for the builder's own use).
-double resp_lowpass(double w);                 // h_hat(w)
-double resp_lowpass_j(int j, double w);        // h_hat_j(w), eq. lowhigh
-double resp_highpass_j(int j, double w);       // g_hat_j(w), eq. lowhigh
-double resp_fan(double w1, double w2);         // P(w1, w2)
+// 1D/2D responses of the filters of design D (null: the built-in closed forms).
+double resp_lowpass(const FilterDesign* D, double w);             // h_hat(w)
+double resp_lowpass_j(const FilterDesign* D, int j, double w);    // h_hat_j(w), eq. lowhigh
+double resp_highpass_j(const FilterDesign* D, int j, double w);   // g_hat_j(w), eq. lowhigh
+double resp_fan(const FilterDesign* D, double w1, double w2);     // P(w1, w2)
+
+// Checks user taps: odd sizes, symmetric h, point-symmetric P (relative 1e-12), sizes
+// h <= 129 and P <= 65 x 65. Returns an empty string or the reason.
+std::string check_design(const FilterDesign& d);
 
 }  // namespace sl

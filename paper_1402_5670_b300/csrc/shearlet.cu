@@ -641,8 +641,32 @@ sl_status sl_build_filters(int ndim, const int64_t* dims, int nScales, const int
 
 sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const int* shearLevels,
                               int fullSystem, int device, const sl_options* opt, sl_bank** out) {
+  return sl_build_filters_user(ndim, dims, nScales, shearLevels, fullSystem, device, opt, nullptr,
+                               out);
+}
+
+sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales, const int* shearLevels,
+                                int fullSystem, int device, const sl_options* opt,
+                                const sl_filters* filters, sl_bank** out) {
   if (!out) return fail(SL_EINVAL, "out is NULL");
   *out = nullptr;
+  std::shared_ptr<sl::FilterDesign> design;
+  if (filters && (filters->qmf || filters->fan)) {
+    design = std::make_shared<sl::FilterDesign>();
+    if (filters->qmf) {
+      if (filters->qmf_len < 1) return fail(SL_EINVAL, "qmf_len must be >= 1");
+      design->h.assign(filters->qmf, filters->qmf + filters->qmf_len);
+    }
+    if (filters->fan) {
+      if (filters->fan_rows < 1 || filters->fan_cols < 1)
+        return fail(SL_EINVAL, "fan_rows and fan_cols must be >= 1");
+      design->pr = filters->fan_rows;
+      design->pc = filters->fan_cols;
+      design->p.assign(filters->fan, filters->fan + (size_t)design->pr * design->pc);
+    }
+    const std::string why = sl::check_design(*design);
+    if (!why.empty()) return fail(SL_EINVAL, why);
+  }
   const int path = opt ? opt->path : SL_PATH_AUTO;
   if (path < SL_PATH_AUTO || path > SL_PATH_CLUSTER) return fail(SL_EINVAL, "unknown path");
   const int prec = opt ? opt->precision : SL_PREC_FP32;
@@ -651,6 +675,7 @@ sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const 
   if (!dims || !shearLevels) return fail(SL_EINVAL, "dims or shearLevels is NULL");
   if (nScales < 1 || nScales > 8) return fail(SL_EINVAL, "nScales must be in [1, 8]");
   sl::BankSpec spec;
+  spec.design = design;
   spec.ndim = ndim;
   spec.J = nScales;
   spec.full = fullSystem != 0;

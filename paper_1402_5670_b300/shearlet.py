@@ -33,6 +33,9 @@ SIGNATURES = {
     "sl_last_error": (ctypes.c_char_p, []),
     "sl_build_filters": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "sl_build_filters_user": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
+                                             ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                             ctypes.POINTER(_vp)]),
     "sl_build_filters_ex": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.POINTER(_vp)]),
@@ -145,6 +148,11 @@ class sl_options(ctypes.Structure):
 PRECISIONS = {"fp32": 0, "tc_bf16": 1}
 
 
+class sl_filters(ctypes.Structure):
+    _fields_ = [("qmf", _c_double_p), ("qmf_len", ctypes.c_int), ("fan", _c_double_p),
+                ("fan_rows", ctypes.c_int), ("fan_cols", ctypes.c_int)]
+
+
 def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
                      full_system: bool = False, device: int = 0) -> int:
     nd = len(dims)
@@ -158,7 +166,9 @@ def sl_build_filters(dims: Sequence[int], n_scales: int, shear_levels: Sequence[
 
 def sl_build_filters_ex(dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
                         full_system: bool = False, device: int = 0, path: str = "auto",
-                        precision: str = "fp32") -> int:
+                        precision: str = "fp32", qmf=None, fan=None) -> int:
+    """sl_build_filters_ex, or sl_build_filters_user when qmf (1D taps) or fan (2D
+    taps) is given."""
     nd = len(dims)
     d = (ctypes.c_int64 * nd)(*[int(v) for v in dims])
     sl = (ctypes.c_int * len(shear_levels))(*[int(v) for v in shear_levels])
@@ -166,8 +176,26 @@ def sl_build_filters_ex(dims: Sequence[int], n_scales: int, shear_levels: Sequen
     opt.path = PATHS[path]
     opt.precision = PRECISIONS[precision]
     out = _vp()
-    _check(lib().sl_build_filters_ex(nd, d, int(n_scales), sl, int(bool(full_system)), int(device),
-                                     ctypes.byref(opt), ctypes.byref(out)), "sl_build_filters_ex")
+    if qmf is None and fan is None:
+        _check(lib().sl_build_filters_ex(nd, d, int(n_scales), sl, int(bool(full_system)),
+                                         int(device), ctypes.byref(opt), ctypes.byref(out)),
+               "sl_build_filters_ex")
+        return out.value
+    f = sl_filters()
+    keep = []
+    if qmf is not None:
+        h = np.ascontiguousarray(qmf, dtype=np.float64).ravel()
+        keep.append(h)
+        f.qmf, f.qmf_len = h.ctypes.data_as(_c_double_p), h.size
+    if fan is not None:
+        P = np.ascontiguousarray(fan, dtype=np.float64)
+        if P.ndim != 2:
+            raise ValueError("fan taps must be a 2D array")
+        keep.append(P)
+        f.fan, f.fan_rows, f.fan_cols = P.ctypes.data_as(_c_double_p), P.shape[0], P.shape[1]
+    _check(lib().sl_build_filters_user(nd, d, int(n_scales), sl, int(bool(full_system)),
+                                       int(device), ctypes.byref(opt), ctypes.byref(f),
+                                       ctypes.byref(out)), "sl_build_filters_user")
     return out.value
 
 
@@ -255,13 +283,13 @@ class Bank:
 
     def __init__(self, dims: Sequence[int], n_scales: int, shear_levels: Sequence[int],
                  full_system: bool = False, device: int = 0, path: str = "auto",
-                 precision: str = "fp32"):
+                 precision: str = "fp32", qmf=None, fan=None):
         if device >= 0:
             import torch
             torch.cuda.set_device(device)
         self.path = path
         self.handle = sl_build_filters_ex(dims, n_scales, shear_levels, full_system, device, path,
-                                          precision)
+                                          precision, qmf, fan)
         L = lib()
         nd, R, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         dd = (ctypes.c_int64 * 3)()
