@@ -1304,6 +1304,7 @@ sl_status sl_inpaint(const sl_bank* cb, const float* f_masked, const uint8_t* ma
                      float delta_init, float delta_min, int iterations, void* stream) {
   SL_TRY(check_call(cb));
   if (!f_masked || !mask || !out) return fail(SL_EINVAL, "f_masked, mask or out is NULL");
+  if ((const void*)out == (const void*)f_masked) return fail(SL_EINVAL, "out must not alias f_masked");
   SL_TRY(check_aligned(f_masked, out));
   if (!a16(mask)) return fail(SL_EINVAL, "device arrays must be 16-byte aligned");
   if (iterations < 1) return fail(SL_EINVAL, "iterations must be >= 1");

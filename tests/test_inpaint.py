@@ -91,6 +91,8 @@ def test_inpaint_rejects_bad_arguments():
                                  10.0, 1.0, 0, None)] == "SL_EINVAL"
     assert S.STATUS[L.sl_inpaint(b.handle, fm.data_ptr(), Mg.data_ptr(), out.data_ptr(),
                                  0.0, 1.0, 3, None)] == "SL_EINVAL"
+    assert S.STATUS[L.sl_inpaint(b.handle, fm.data_ptr(), Mg.data_ptr(), fm.data_ptr(),
+                                 10.0, 1.0, 3, None)] == "SL_EINVAL"
     mbuf = torch.zeros(b.N + 16, dtype=torch.uint8, device="cuda")
     assert S.STATUS[L.sl_inpaint(b.handle, fm.data_ptr(), mbuf.data_ptr() + 1, out.data_ptr(),
                                  10.0, 1.0, 3, None)] == "SL_EINVAL"
