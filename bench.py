@@ -399,16 +399,24 @@ def extras(b, x, clean, C, flush, args):
     fl_fwd = 2 * (F * 64 + 64 * 64 + 64)
     learned.train(mlp, pairs, steps=2000, batch=32768, lr=3e-3, seed=1)
     Ca = torch.empty_like(C)
+    mlp.set_engine("mma_sync")
+    ms_m = _time_graph(lambda: mlp.apply(C, SIGMA, out=Ca), flush, steps)
+    mlp.set_engine("tcgen05")
     ms_i = _time_graph(lambda: mlp.apply(C, SIGMA, out=Ca), flush, steps)
+    mlp.check()
     ymlp = mlp.denoise(x, SIGMA)
     out["mlp_shrinkage"] = {
         "train_step_ms": ms_t, "train_samples_per_s": batch / (ms_t * 1e-3),
         "train_tflops": 3 * fl_fwd * batch / (ms_t * 1e-3) / 1e12,
         "infer_ms": ms_i, "infer_coeffs_per_s": (R - 1) * N / (ms_i * 1e-3),
         "infer_tflops": fl_fwd * (R - 1) * N / (ms_i * 1e-3) / 1e12,
+        "infer_alg_bytes": 8 * R * N,
+        "infer_frac_hbm": 8 * R * N / (ms_i * 1e-3) / 1e9 / peak,
+        "infer_ms_mma_sync": ms_m,
         "psnr_learned": sl_error_stats(ymlp, cl)["psnr"],
-        "note": "BF16 mma.sync tensor cores, FP32 accumulate; flops count the two "
-                "dense layers and the output dot (backward ~2x forward)"}
+        "note": "inference on tcgen05 (128-row tiles, TMEM accumulators), training on "
+                "BF16 mma.sync, FP32 accumulate; flops count the two dense layers and "
+                "the output dot (backward ~2x forward)"}
     try:
         out["inpaint_random80_300it"] = inpaint_run(b, clean)
     except Exception as e:  # report, do not fail the headline line

@@ -393,6 +393,19 @@ sl_status sl_mlp_train_step(sl_mlp* mlp, const float* noisy, const float* clean,
 /* out[j] = g * coeffs[j] for every subband j >= 1 and out[0] = coeffs[0] (DEVICE
  * [R][dims]; out must not alias coeffs, whose neighbourhoods the features read). */
 sl_status sl_mlp_apply(sl_mlp* mlp, const float* coeffs, float* out, float sigma, void* stream);
+/* Inference engine of sl_mlp_apply: SL_MLP_TCGEN05 (default) runs both layers as
+ * tcgen05.mma on tiles of 128 coefficients with the accumulators in tensor memory;
+ * SL_MLP_MMA_SYNC runs them as warp-level mma.sync on tiles of 16 (the kernel the
+ * training step shares). Same BF16 operands and FP32 accumulation; sums may round in
+ * another order. SL_EINVAL for another value. */
+#define SL_MLP_TCGEN05 0
+#define SL_MLP_MMA_SYNC 1
+sl_status sl_mlp_set_engine(sl_mlp* mlp, int engine);
+/* Synchronises the stream and reports whether a tensor-core wait of an earlier
+ * sl_mlp_apply ran out (each wait gives up after about two seconds, sets a device flag
+ * and the kernel returns with that tile's output unwritten): SL_ECUDA and the flag
+ * cleared if so, SL_OK otherwise. */
+sl_status sl_mlp_check(sl_mlp* mlp, void* stream);
 /* Learned denoising: sl_forward, sl_mlp_apply, sl_inverse (DEVICE [dims] arrays; the
  * first call allocates 2 R N floats of coefficient memory kept by the MLP). */
 sl_status sl_mlp_denoise(sl_mlp* mlp, const float* noisy, float* out, float sigma, void* stream);

@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -267,6 +268,410 @@ __global__ void __launch_bounds__(32 * WARPS) k_mlp_apply(MlpArgs a) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.geo.N;
          i += (int64_t)gridDim.x * blockDim.x)
       a.out[i] = a.C[i];
+}
+
+// ---------------------------------------------- inference on tcgen05 tensor cores ---
+// Tiles of 128 coefficients: one CTA of 4 warps, thread t builds the features of row t
+// (BF16, in shared memory), one thread issues tcgen05.mma for the two dense layers
+// with the accumulator in tensor memory (128 lanes = rows, 64 FP32 columns, reused by
+// both layers), and every warp reads its 32 rows back with tcgen05.ld for bias, ReLU,
+// the output dot and the gain. The raw neighbourhood of the next tile is loaded into
+// registers while the current tile is in the tensor cores, so global-memory latency
+// overlaps the products and the epilogues.
+// Operands are K-major without swizzle: 8 x 16-byte core matrices, element (r, k) of a
+// [rows][K] tile at ((r / 8) (K / 8) + k / 8) 128 + (r % 8) 16 + (k % 8) 2 bytes, so the
+// descriptors' leading (K) offset is 128 B and the stride (row block) offset (K / 8) 128 B.
+constexpr int TC_ROWS = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_TMEM_COLS = 64;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ int kmajor(int r, int k, int K) {
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// tcgen05 shared-memory matrix descriptor: start, leading and stride byte offsets
+// (all >> 4), the fixed descriptor version 1 at bit 46, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
+// N = 64, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_addr(bar)));
+}
+
+// Bounded wait for the mbarrier phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  const long long t0 = clock64();
+  while (!done) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity));
+    if (!done && clock64() - t0 > 4000000000LL) return false;  // about two seconds
+  }
+  return true;
+}
+
+// 32 FP32 accumulator columns of this thread's TMEM lane (warp w owns lanes 32w..).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// generic-proxy shared-memory writes -> visible to the tensor cores' reads
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ReLU and round to BF16, two values packed (lo in the low half)
+__device__ __forceinline__ uint32_t relu_pack_bf16(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// The biases ride in the products: b = hi + lo (two BF16 parts, |b - hi - lo| <=
+// 2^-16 |b|) occupy two extra K columns of W1 and W2, against two constant-one
+// columns of the activations, so the epilogues read no bias.
+constexpr int K2 = H + 16;  // layer-2 K: h1, [1, 1], zero padding
+
+// The weights of one CTA as its shared memory holds them, packed once per call by
+// k_mlp_pack_tc and copied by every CTA with 16-byte loads.
+template <int NDIM>
+struct TcWeights {
+  static constexpr int KP = Net<NDIM>::KP;
+  static_assert(Net<NDIM>::F + 2 <= KP, "two bias columns after the features");
+  // operand tiles without swizzle need only 16-byte alignment
+  alignas(16) unsigned char w1[H * KP * 2];  // [W1, b1 hi, b1 lo, 0..] [64][KP]
+  alignas(16) unsigned char w2[H * K2 * 2];  // [W2, b2 hi, b2 lo, 0..] [64][K2]
+  alignas(16) float w3[H];
+  alignas(16) float b3[4];
+};
+
+template <int NDIM>
+struct TcApplySmem {
+  static_assert(Net<NDIM>::KP <= K2, "the layer-1 operand shares the layer-2 buffer");
+  static_assert(sizeof(TcWeights<NDIM>) % 16 == 0, "copied in 16-byte pieces");
+  TcWeights<NDIM> w;
+  // act holds the features [128][KP] for layer 1, then [h1, 1, 1, 0..] [128][K2]
+  alignas(16) unsigned char act[TC_ROWS * K2 * 2];
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
+};
+
+// FP32 master parameters -> the BF16 K-major weight tiles of TcWeights, one element
+// per thread over w1, w2, w3 and b3 in turn.
+template <int NDIM>
+constexpr int tc_pack_elems() { return H * Net<NDIM>::KP + H * K2 + H + 4; }
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) k_mlp_pack_tc(const float* __restrict__ prm,
+                                                     TcWeights<NDIM>* __restrict__ out) {
+  using NN = Net<NDIM>;
+  constexpr int F = NN::F, KP = NN::KP;
+  auto split = [](float b, bool lo_part) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+    return lo_part ? __float2bfloat16_rn(b - __bfloat162float(hi)) : hi;
+  };
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < H * KP) {
+    const int o = i / KP, k = i % KP;
+    __nv_bfloat16 w = __float2bfloat16_rn(0.f);
+    if (k < F) w = __float2bfloat16_rn(prm[NN::oW1 + o * F + k]);
+    else if (k < F + 2) w = split(prm[NN::ob1 + o], k == F + 1);
+    *reinterpret_cast<__nv_bfloat16*>(out->w1 + kmajor(o, k, KP)) = w;
+    return;
+  }
+  i -= H * KP;
+  if (i < H * K2) {
+    const int o = i / K2, k = i % K2;
+    __nv_bfloat16 w = __float2bfloat16_rn(0.f);
+    if (k < H) w = __float2bfloat16_rn(prm[NN::oW2 + o * H + k]);
+    else if (k < H + 2) w = split(prm[NN::ob2 + o], k == H + 1);
+    *reinterpret_cast<__nv_bfloat16*>(out->w2 + kmajor(o, k, K2)) = w;
+    return;
+  }
+  i -= H * K2;
+  if (i < H) {
+    out->w3[i] = prm[NN::ow3 + i];
+    return;
+  }
+  i -= H;
+  if (i < 4) out->b3[i] = i == 0 ? prm[NN::ob3] : 0.f;
+}
+
+// Read-only global load that the compiler keeps where it is written (a prefetch a
+// tile ahead must not sink to its first use).
+__device__ __forceinline__ float ld_early(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
+// The raw neighbourhood of point m of one subband (nb in the row-major order of
+// {-1, 0, 1}^ndim that neighbour() uses), with the periodic wrap taken once per axis.
+template <int NDIM>
+__device__ __forceinline__ void gather_nb(const Geom& g, const float* __restrict__ sub, uint32_t m,
+                                          float (&nb)[Net<NDIM>::NB]) {
+  if constexpr (NDIM == 2) {
+    const uint32_t m0 = g.dims[0] - 1, m1 = g.dims[1] - 1;
+    const uint32_t i0 = m >> g.lg[1], i1 = m & m1;
+    const uint32_t r[3] = {((i0 - 1) & m0) << g.lg[1], i0 << g.lg[1], ((i0 + 1) & m0) << g.lg[1]};
+    const uint32_t c[3] = {(i1 - 1) & m1, i1, (i1 + 1) & m1};
+#pragma unroll
+    for (int a0 = 0; a0 < 3; ++a0)
+#pragma unroll
+      for (int a1 = 0; a1 < 3; ++a1) nb[3 * a0 + a1] = ld_early(sub + (r[a0] + c[a1]));
+  } else {
+    const uint32_t m0 = g.dims[0] - 1, m1 = g.dims[1] - 1, m2 = g.dims[2] - 1;
+    const int s0 = g.lg[1] + g.lg[2];
+    const uint32_t i0 = m >> s0, i1 = (m >> g.lg[2]) & m1, i2 = m & m2;
+    const uint32_t pl[3] = {((i0 - 1) & m0) << s0, i0 << s0, ((i0 + 1) & m0) << s0};
+    const uint32_t r[3] = {((i1 - 1) & m1) << g.lg[2], i1 << g.lg[2], ((i1 + 1) & m1) << g.lg[2]};
+    const uint32_t c[3] = {(i2 - 1) & m2, i2, (i2 + 1) & m2};
+#pragma unroll
+    for (int a0 = 0; a0 < 3; ++a0)
+#pragma unroll
+      for (int a1 = 0; a1 < 3; ++a1) {
+        const uint32_t pr = pl[a0] + r[a1];
+#pragma unroll
+        for (int a2 = 0; a2 < 3; ++a2) nb[9 * a0 + 3 * a1 + a2] = ld_early(sub + (pr + c[a2]));
+      }
+  }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_mlp_apply_tc(MlpArgs a, const TcWeights<NDIM>* __restrict__ wg, int* err) {
+  using NN = Net<NDIM>;
+  constexpr int F = NN::F, KP = NN::KP, NB = NN::NB;
+  constexpr int CENTRE = NB / 2;  // offset (0, .., 0) in the row-major neighbourhood
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TcApplySmem<NDIM>& S = *reinterpret_cast<TcApplySmem<NDIM>*>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // Tensor memory first: the SM starts its next CTA only once this one has given up
+  // its allocation permit.
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&S.tmem)),
+                 "n"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  {
+    constexpr int n16 = (int)(sizeof(TcWeights<NDIM>) / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(wg);
+    uint4* dst = reinterpret_cast<uint4*>(&S.w);
+    for (int i = tid; i < n16; i += TC_THREADS) dst[i] = __ldg(src + i);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  fence_async_smem();  // the weight tiles are read by the tensor cores
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const float* E = a.prm + NN::oE;
+  const int64_t total = (int64_t)(a.R - 1) * a.geo.N;
+  const int64_t tiles = (total + TC_ROWS - 1) / TC_ROWS;
+  const uint32_t act = smem_addr(S.act), w1 = smem_addr(S.w.w1), w2 = smem_addr(S.w.w2);
+  const int lgN = a.geo.lg[0] + a.geo.lg[1] + a.geo.lg[2];
+  constexpr uint32_t kOnes = 0x3F803F80u;  // two BF16 ones
+  // raw neighbourhood of this thread's row, gathered one tile ahead (rows past the
+  // end read coefficient N); N = 2^lgN points per subband (sizes are powers of two)
+  float nb[NB];
+  auto gather = [&](int64_t t) {
+    const int64_t idx = t * TC_ROWS + tid;
+    const int64_t q = a.geo.N + (t < tiles && idx < total ? idx : 0);
+    gather_nb<NDIM>(a.geo, a.C + ((q >> lgN) << lgN), (uint32_t)(q & (a.geo.N - 1)), nb);
+  };
+  gather(blockIdx.x);
+  // Each tile completes two phases of the mbarrier: layer 1 (parity 0), layer 2
+  // (parity 1). Every thread waits on both, so none lags a phase behind; a wait that
+  // runs out is made CTA-uniform at the next barrier, and the loop ends there.
+  int timed_out = 0;     // CTA-uniform
+  uint32_t pending = 0;  // parity of the phase a timed-out wait left in flight
+  bool late = false;     // this warp's last wait ran out (warp-uniform)
+  for (int64_t t = blockIdx.x;; t += gridDim.x) {
+    const bool more = t < tiles;
+    const int64_t idx = t * TC_ROWS + tid;
+    const bool valid = more && idx < total;
+    const int64_t q = a.geo.N + (valid ? idx : 0);  // other rows compute on coefficient N
+    float c = 0.f;
+    if (more) {
+      const int j = (int)(q >> lgN);
+      c = nb[CENTRE];
+      const float is = a.inv_s[j];
+      // features of this thread's row, the two bias ones -> act (8 BF16 per store)
+      float x[KP];
+      x[0] = c * is;
+#pragma unroll
+      for (int d = 0; d < NB; ++d) x[1 + d] = fabsf(nb[d]) * is;
+#pragma unroll
+      for (int e = 0; e < EMB; ++e) x[1 + NB + e] = __ldg(E + j * EMB + e);
+      x[F] = 1.f;
+      x[F + 1] = 1.f;
+#pragma unroll
+      for (int k = F + 2; k < KP; ++k) x[k] = 0.f;
+#pragma unroll
+      for (int k8 = 0; k8 < KP / 8; ++k8)
+        *reinterpret_cast<uint4*>(S.act + kmajor(tid, 8 * k8, KP)) =
+            make_uint4(pack_bf16(x[8 * k8], x[8 * k8 + 1]), pack_bf16(x[8 * k8 + 2], x[8 * k8 + 3]),
+                       pack_bf16(x[8 * k8 + 4], x[8 * k8 + 5]),
+                       pack_bf16(x[8 * k8 + 6], x[8 * k8 + 7]));
+    }
+    fence_async_smem();
+    tc_before_sync();
+    // features written, previous tile's TMEM reads done; any earlier timeout seen
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 1;
+      break;
+    }
+    tc_after_sync();
+    if (!more) break;
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KP / 16; ++ks)
+        umma_bf16(tmem, umma_desc(act + ks * 256, 128, (KP / 8) * 128),
+                  umma_desc(w1 + ks * 256, 128, (KP / 8) * 128), ks > 0);
+      umma_commit(&S.bar);
+    }
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0));
+    tc_after_sync();
+    if (!late) {
+      // h1 = relu(z1) -> act, 32 columns at a time, then the bias ones
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float z[32];
+        tmem_ld32(tmem + lane_base + 32 * h, z);
+#pragma unroll
+        for (int k8 = 0; k8 < 4; ++k8)
+          *reinterpret_cast<uint4*>(S.act + kmajor(tid, 32 * h + 8 * k8, K2)) =
+              make_uint4(relu_pack_bf16(z[8 * k8], z[8 * k8 + 1]),
+                         relu_pack_bf16(z[8 * k8 + 2], z[8 * k8 + 3]),
+                         relu_pack_bf16(z[8 * k8 + 4], z[8 * k8 + 5]),
+                         relu_pack_bf16(z[8 * k8 + 6], z[8 * k8 + 7]));
+      }
+      *reinterpret_cast<uint4*>(S.act + kmajor(tid, H, K2)) = make_uint4(kOnes, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(S.act + kmajor(tid, H + 8, K2)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    fence_async_smem();
+    tc_before_sync();
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 0;
+      break;
+    }
+    tc_after_sync();
+    gather(t + gridDim.x);  // the next tile's loads overlap layer 2
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < K2 / 16; ++ks)
+        umma_bf16(tmem, umma_desc(act + ks * 256, 128, (K2 / 8) * 128),
+                  umma_desc(w2 + ks * 256, 128, (K2 / 8) * 128), ks > 0);
+      umma_commit(&S.bar);
+    }
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1));
+    tc_after_sync();
+    if (!late) {
+      float acc[4] = {S.w.b3[0], 0.f, 0.f, 0.f};  // four chains of 16
+      const float4* w3 = reinterpret_cast<const float4*>(S.w.w3);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float z[32];
+        tmem_ld32(tmem + lane_base + 32 * h, z);
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 w = w3[8 * h + k4];
+          acc[0] += fmaxf(z[4 * k4], 0.f) * w.x;
+          acc[1] += fmaxf(z[4 * k4 + 1], 0.f) * w.y;
+          acc[2] += fmaxf(z[4 * k4 + 2], 0.f) * w.z;
+          acc[3] += fmaxf(z[4 * k4 + 3], 0.f) * w.w;
+        }
+      }
+      const float g = 1.f / (1.f + expf(-((acc[0] + acc[1]) + (acc[2] + acc[3]))));
+      if (valid) a.out[q] = g * c;
+    }
+  }
+  if (timed_out) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mbar_wait(&S.bar, pending);  // let the MMAs in flight finish (bounded) before the free
+    }
+    __syncthreads();
+  }
+  // the lowpass passes through
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.geo.N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a.out[i] = a.C[i];
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "n"(TC_TMEM_COLS));
+}
+
+// Persistent grid: every SM holds as many CTAs as its registers, shared memory and
+// tensor memory (TC_TMEM_COLS of 512 columns each) allow. (The occupancy calculator
+// is not used: for this kernel it reports one CTA per SM, below what runs.)
+template <int NDIM>
+static int apply_tc_grid() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 148, smem_sm = 228 * 1024, regs_sm = 65536;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_mlp_apply_tc<NDIM>);
+    const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8) * TC_THREADS;
+    const int smem = (int)sizeof(TcApplySmem<NDIM>) + 1024;  // + the per-CTA reserve
+    int per_sm = std::min({512 / TC_TMEM_COLS, smem_sm / smem, regs_sm / regs});
+    grid = std::max(1, per_sm) * sms;
+  }
+  return grid;
 }
 
 // Training: forward and backward on a sample; gradients accumulate into a.grad.
@@ -576,6 +981,11 @@ struct sl_mlp {
   float* v = nullptr;
   float* loss = nullptr;
   float* inv_s = nullptr;  // [R]
+  int* tc_err = nullptr;   // set by a tensor-core wait that ran out
+  void* tc_pack = nullptr; // BF16 weight tiles of the tcgen05 inference kernel
+  bool tc_packed = false;  // tc_pack holds the current parameters (packed on pack_stream)
+  cudaStream_t pack_stream = nullptr;
+  int engine = SL_MLP_TCGEN05;
   float* coeffs = nullptr; // [2][R][N] for sl_mlp_denoise (allocated on first use)
   std::vector<double> norms;
   int t = 0;
@@ -640,8 +1050,12 @@ sl_status sl_mlp_create(const sl_bank* bank, sl_mlp** out) {
             cudaMalloc(&M->m, M->P * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->v, M->P * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->loss, sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&M->inv_s, R * sizeof(float)) == cudaSuccess;
+            cudaMalloc(&M->inv_s, R * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&M->tc_err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&M->tc_pack, std::max(sizeof(TcWeights<2>), sizeof(TcWeights<3>))) ==
+                cudaSuccess;
   if (ok) ok = cudaMemset(M->prm, 0, M->P * sizeof(float)) == cudaSuccess &&
+               cudaMemset(M->tc_err, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(M->m, 0, M->P * sizeof(float)) == cudaSuccess &&
                cudaMemset(M->v, 0, M->P * sizeof(float)) == cudaSuccess;
   if (!ok) {
@@ -661,6 +1075,8 @@ void sl_mlp_free(sl_mlp* M) {
   cudaFree(M->v);
   cudaFree(M->loss);
   cudaFree(M->inv_s);
+  cudaFree(M->tc_err);
+  cudaFree(M->tc_pack);
   cudaFree(M->coeffs);
   delete M;
 }
@@ -669,6 +1085,7 @@ int sl_mlp_num_params(const sl_mlp* M) { return M ? M->P : 0; }
 
 sl_status sl_mlp_set_params(sl_mlp* M, const float* host) {
   if (!M || !host) return mfail(SL_EINVAL, "NULL argument");
+  M->tc_packed = false;
   if (cudaMemcpy(M->prm, host, M->P * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
     return mfail(SL_ECUDA, "cudaMemcpy");
   cudaMemset(M->m, 0, M->P * sizeof(float));
@@ -722,6 +1139,7 @@ sl_status sl_mlp_load(sl_mlp* M, const char* path) {
   ok = ok && std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
   std::fclose(f);
   if (!ok) return mfail(SL_EINVAL, std::string(path) + " is not a complete MLP checkpoint");
+  M->tc_packed = false;
   if (cudaMemcpy(M->prm, buf.data(), M->P * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(M->m, buf.data() + M->P, M->P * sizeof(float), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
@@ -791,6 +1209,7 @@ sl_status sl_mlp_train_step(sl_mlp* M, const float* noisy, const float* clean, f
   if (s != SL_OK) return s;
   M->t += 1;
   const float c1 = 1.f - std::pow(0.9f, (float)M->t), c2 = 1.f - std::pow(0.999f, (float)M->t);
+  M->tc_packed = false;
   k_adam<<<(M->P + 255) / 256, 256, 0, st>>>(M->prm, M->grad, M->m, M->v, M->P, lr, c1, c2);
   if (loss_dev &&
       cudaMemcpyAsync(loss_dev, M->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -813,18 +1232,63 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
   a.inv_s = M->inv_s;
   a.geo = M->geo;
   a.R = M->R;
-  const int grid = 4 * 148;
-  if (M->ndim == 2) {
-    const size_t sm = apply_smem<2>();
-    cudaFuncSetAttribute(k_mlp_apply<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_mlp_apply<2><<<grid, 32 * WARPS, sm, st>>>(a);
+  if (M->engine == SL_MLP_TCGEN05) {
+    // the grid keeps every SM's CTAs within its 512 TMEM columns: no allocation waits
+    if (M->ndim == 2) {
+      const size_t sm = sizeof(TcApplySmem<2>);
+      cudaFuncSetAttribute(k_mlp_apply_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_mlp_apply_tc<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      auto* wt = reinterpret_cast<TcWeights<2>*>(M->tc_pack);
+      if (!M->tc_packed || M->pack_stream != st)
+        k_mlp_pack_tc<2><<<(tc_pack_elems<2>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
+      k_mlp_apply_tc<2><<<apply_tc_grid<2>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
+    } else {
+      const size_t sm = sizeof(TcApplySmem<3>);
+      cudaFuncSetAttribute(k_mlp_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_mlp_apply_tc<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      auto* wt = reinterpret_cast<TcWeights<3>*>(M->tc_pack);
+      if (!M->tc_packed || M->pack_stream != st)
+        k_mlp_pack_tc<3><<<(tc_pack_elems<3>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
+      k_mlp_apply_tc<3><<<apply_tc_grid<3>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
+    }
   } else {
-    const size_t sm = apply_smem<3>();
-    cudaFuncSetAttribute(k_mlp_apply<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_mlp_apply<3><<<grid, 32 * WARPS, sm, st>>>(a);
+    const int grid = 4 * 148;
+    if (M->ndim == 2) {
+      const size_t sm = apply_smem<2>();
+      cudaFuncSetAttribute(k_mlp_apply<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_mlp_apply<2><<<grid, 32 * WARPS, sm, st>>>(a);
+    } else {
+      const size_t sm = apply_smem<3>();
+      cudaFuncSetAttribute(k_mlp_apply<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_mlp_apply<3><<<grid, 32 * WARPS, sm, st>>>(a);
+    }
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_mlp_apply: ") + cudaGetErrorString(e));
+  if (M->engine == SL_MLP_TCGEN05) {
+    M->tc_packed = true;
+    M->pack_stream = st;
+  }
+  return SL_OK;
+}
+
+sl_status sl_mlp_set_engine(sl_mlp* M, int engine) {
+  if (!M) return mfail(SL_EINVAL, "NULL argument");
+  if (engine != SL_MLP_TCGEN05 && engine != SL_MLP_MMA_SYNC) return mfail(SL_EINVAL, "unknown engine");
+  M->engine = engine;
+  return SL_OK;
+}
+
+sl_status sl_mlp_check(sl_mlp* M, void* stream) {
+  if (!M) return mfail(SL_EINVAL, "NULL argument");
+  int h = 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+      cudaMemcpy(&h, M->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mfail(SL_ECUDA, std::string("sl_mlp_check: ") + cudaGetErrorString(cudaGetLastError()));
+  if (h) {
+    cudaMemset(M->tc_err, 0, sizeof(int));
+    return mfail(SL_ECUDA, "a tensor-core wait of sl_mlp_apply ran out (its output is incomplete)");
+  }
   return SL_OK;
 }
 

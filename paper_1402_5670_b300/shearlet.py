@@ -81,6 +81,8 @@ SIGNATURES = {
     "sl_mlp_last_error": (ctypes.c_char_p, []),
     "sl_mlp_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "sl_mlp_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "sl_mlp_set_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "sl_mlp_check": (ctypes.c_int, [_vp, _vp]),
     "sl_error_stats": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _c_double_p, _vp]),
     "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sl_profile_reset": (ctypes.c_int, []),
@@ -425,6 +427,9 @@ def _mcheck(status: int, where: str) -> None:
         raise ShearletError(status, where, lib().sl_mlp_last_error().decode(errors="replace"))
 
 
+MLP_ENGINES = {"tcgen05": 0, "mma_sync": 1}
+
+
 class MLP:
     """Learned shrinkage bound to a device Bank (sl_mlp_*)."""
 
@@ -486,6 +491,16 @@ class MLP:
                                    _dev_ptr(out, "out", n_all), float(sigma),
                                    _stream_ptr(stream)), "sl_mlp_apply")
         return out
+
+    def set_engine(self, engine: str):
+        """'tcgen05' (default) or 'mma_sync': the tensor-core path of apply."""
+        if engine not in MLP_ENGINES:
+            raise ValueError(f"engine must be one of {sorted(MLP_ENGINES)}")
+        _mcheck(lib().sl_mlp_set_engine(self.handle, MLP_ENGINES[engine]), "sl_mlp_set_engine")
+
+    def check(self, stream=None):
+        """Synchronise and raise if a tensor-core wait of an earlier apply ran out."""
+        _mcheck(lib().sl_mlp_check(self.handle, _stream_ptr(stream)), "sl_mlp_check")
 
     def denoise(self, noisy, sigma: float, out=None, stream=None):
         out = self.bank._empty(self.bank.dims) if out is None else out

@@ -159,17 +159,58 @@ def test_gpu_gradients_match_oracle(case):
 
 
 @pytest.mark.gpu
-def test_gpu_apply_matches_oracle():
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("case", [((64, 64), 2, (1, 1)), ((16, 16, 16), 1, (0,))], ids=str)
+def test_gpu_apply_matches_oracle(case, engine):
+    """Inference on both engines (tcgen05 tiles of 128 rows with TMEM accumulators,
+    and warp-level mma.sync) against the oracle with the same BF16 operand rounding.
+    Supported sizes make (R - 1) N a multiple of 128, so every tcgen05 tile is full."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    dims, J, sl = (64, 64), 2, (1, 1)
+    dims, J, sl = case
     b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 4)
+    mlp.set_engine(engine)
     s_sys = oracle_system(dims, J, sl)
-    out = mlp.apply(Cn, 20.0).cpu().numpy()
-    p = M.unflatten(flat.astype(np.float64), 2, b.R)
+    out = mlp.apply(Cn, 20.0)
+    mlp.check()
+    out = out.cpu().numpy()
+    p = M.unflatten(flat.astype(np.float64), len(dims), b.R)
     ref = M.apply(p, Cn.cpu().numpy().astype(np.float64), 20.0 * s_sys.norms, bf16_operands=True)
     assert np.array_equal(out[0], Cn[0].cpu().numpy())
     assert np.max(np.abs(out - ref)) <= 2e-3 * np.max(np.abs(ref))
+
+
+@pytest.mark.gpu
+def test_gpu_apply_engines_agree_at_full_size():
+    """512^2, 49 subbands: the two engines agree coefficient by coefficient (same BF16
+    operands, FP32 sums in another order), and sampled coefficients match the oracle
+    computed one by one."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dims, J, sl = (512, 512), 4, (1, 1, 2, 2)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 6)
+    mlp.set_engine("tcgen05")
+    a = mlp.apply(Cn, 20.0)
+    mlp.check()
+    mlp.set_engine("mma_sync")
+    m = mlp.apply(Cn, 20.0)
+    torch.cuda.synchronize()
+    scale = float(Cn.abs().max())
+    assert float((a - m).abs().max()) <= 2e-3 * scale
+    assert torch.equal(a[0], Cn[0])
+    s_sys = oracle_system(dims, J, sl)
+    r = np.random.default_rng(9)
+    q = r.integers(b.N, b.R * b.N, 4096)
+    j = q // b.N
+    mm = np.stack(np.unravel_index(q % b.N, dims), 1)
+    p = M.unflatten(flat.astype(np.float64), 2, b.R)
+    C = Cn.cpu().numpy().astype(np.float64)
+    s = 20.0 * s_sys.norms
+    X = M.features(C, j, mm, s, p["E"])
+    g, _ = M.forward(p, X, bf16_operands=True)
+    want = g * C[(j,) + tuple(mm.T)]
+    got = a.cpu().numpy()[(j,) + tuple(mm.T)]
+    assert np.max(np.abs(got - want)) <= 2e-3 * scale
 
 
 @pytest.mark.gpu
