@@ -2,8 +2,10 @@
 // coefficient from the coefficient, its neighbourhood magnitudes and a learned
 // subband embedding, replacing the hard threshold of the paper's denoiser
 // (eq. hard_tresholding, Sec. 5.3). Training (forward, backward, Adam) and inference
-// run in these kernels; the products run on the tensor cores as BF16 mma.sync with
-// FP32 accumulation, master weights stay FP32.
+// run in these kernels; the products run on the tensor cores in BF16 with FP32
+// accumulation (training: warp-level mma.sync with the activations in registers;
+// inference: tcgen05.mma on 128-row tiles with the accumulators in tensor memory, or
+// mma.sync as a second engine), master weights stay FP32.
 //
 // Network (F = 1 + 3^ndim + 8 features, padded to KP = F rounded up to 16):
 //   x = [c/s, |c(m+d)|/s for d in {-1,0,1}^ndim (row-major, periodic), E_j]
