@@ -443,11 +443,51 @@ def extras(b, x, clean, C, flush, args):
             "ms": ms3, "coeffs_per_s": b3.R * b3.N / (ms3 * 1e-3), "R": b3.R,
             "alg_bytes": alg3, "frac_hbm": alg3 / (ms3 * 1e-3) / 1e9 / peak,
             "rel_err_reconstruction": float((y3 - xv).abs().max() / xv.abs().max())}
+        try:
+            out["mlp_3d_128"] = mlp_3d(b3, xv, C3, flush, max(3, steps // 3))
+        except Exception as e:  # report, do not fail the headline line
+            out["mlp_3d_128"] = {"error": str(e)}
         del C3
         b3.close()
     except Exception as e:  # report, do not fail the headline line
         out["3d_128_fwd_inv"] = {"error": str(e)}
     return out
+
+
+def mlp_3d(b3, xv, C3, flush, steps) -> dict:
+    """Learned shrinkage on the 128^3 bank (R = 292, 6.1e8 coefficients): inference
+    on both engines and one training step (65,536 samples), random-init weights."""
+    import torch
+    from paper_1402_5670_b300 import synth
+    from paper_1402_5670_b300.shearlet import MLP
+    vc = torch.from_numpy(synth.moving_ellipses_volume((128, 128, 128), SEED)).cuda()
+    Cc3 = b3.forward(vc)
+    b3.forward(xv, out=C3)
+    m3 = MLP(b3)
+    m3.set_params(synth.mlp_init(3, b3.R, 12))
+    O3 = torch.empty_like(C3)
+    m3.set_engine("mma_sync")
+    ms_m = _time_graph(lambda: m3.apply(C3, SIGMA, out=O3), flush, steps)
+    m3.set_engine("tcgen05")
+    ms_t = _time_graph(lambda: m3.apply(C3, SIGMA, out=O3), flush, steps)
+    m3.check()
+    n_sub = (b3.R - 1) * b3.N
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    batch = 65536
+    idx = (torch.randint(0, n_sub, (batch,), generator=gen, device="cuda") + b3.N).to(torch.int32)
+    ms_tr = _time_graph(lambda: m3.train_step(C3, Cc3, SIGMA, idx, 1e-4), flush, steps)
+    F = 1 + 27 + 8
+    fl_fwd = 2 * (F * 64 + 64 * 64 + 64)
+    m3.close()
+    del Cc3, O3
+    return {"infer_ms": ms_t, "infer_coeffs_per_s": n_sub / (ms_t * 1e-3),
+            "infer_tflops": fl_fwd * n_sub / (ms_t * 1e-3) / 1e12,
+            "infer_ms_mma_sync": ms_m,
+            "train_step_ms": ms_tr, "train_samples_per_s": batch / (ms_tr * 1e-3),
+            "train_tflops": 3 * fl_fwd * batch / (ms_tr * 1e-3) / 1e12,
+            "note": "3x3x3 neighbourhood features (F = 36); flops count the two dense layers "
+                    "and the output dot"}
 
 
 def inpaint_run(b, clean) -> dict:
