@@ -523,19 +523,21 @@ def inpaint_run(b, clean) -> dict:
 
 def tc_vs_fp32(b, x, flush, steps: int, peak: float) -> dict:
     """The same 512^2 forward + inverse with the pencil passes on the tensor cores
-    (split BF16, FP32 accumulate) and in FP32, each with its error against an FP64
+    (split BF16 or split FP16 with block scaling, FP32 accumulate) and in FP32, each
+    with its error against an FP64
     evaluation (numpy FFTs in double precision with the bank's FP64 filters, for a
     sample of subbands) and its reconstruction error."""
     import numpy as np
     import torch
     from paper_1402_5670_b300.shearlet import Bank
     bt = Bank(DIMS, J, LEVELS, device=b.device, precision="tc_bf16")
+    bh = Bank(DIMS, J, LEVELS, device=b.device, precision="tc_fp16")
     xd = x.cpu().numpy().astype(np.float64)
     X = np.fft.rfft2(xd)
     js = (0, 7, 24, 48)
     ref = {j: np.fft.irfft2(X * b.eval_f64(j), s=DIMS) for j in js}
     res = {}
-    for name, bk in (("fp32", b), ("tc_bf16", bt)):
+    for name, bk in (("fp32", b), ("tc_bf16", bt), ("tc_fp16", bh)):
         C = torch.empty((bk.R,) + DIMS, device="cuda")
         y = torch.empty_like(x)
         ms = _time_graph(lambda: (bk.forward(x, out=C), bk.inverse(C, out=y)), flush, steps)
@@ -549,6 +551,7 @@ def tc_vs_fp32(b, x, flush, steps: int, peak: float) -> dict:
         del C
     res["error_sample"] = f"subbands {list(js)}, max-abs error / max-abs FP64 value"
     bt.close()
+    bh.close()
     return res
 
 

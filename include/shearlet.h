@@ -104,12 +104,16 @@ typedef struct {
    *                    split operands (hi + lo) and FP32 accumulation; error vs FP64
    *                    about 1e-5 relative. Needs the general path and n0 a power
    *                    of two in [64, 1024] (SL_ENOTSUP otherwise).
+   *   SL_PREC_TC_FP16  the same stages with FP16 operands (hi + lo, about 22 bits);
+   *                    each warp's operand block is scaled by a power of two into
+   *                    FP16's range first; error vs FP64 about 1e-6 relative. Same
+   *                    requirements as SL_PREC_TC_BF16.
    * The last-axis passes, the single-signal FFTs and the FP64 division by Psi are
-   * the same in both modes. */
+   * the same in every mode. */
   int precision;
   int reserved[6];
 } sl_options;
-enum { SL_PREC_FP32 = 0, SL_PREC_TC_BF16 = 1 };
+enum { SL_PREC_FP32 = 0, SL_PREC_TC_BF16 = 1, SL_PREC_TC_FP16 = 2 };
 
 /* sl_build_filters with options (opt may be NULL: defaults). */
 sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales,
@@ -166,7 +170,7 @@ sl_status sl_bank_norms(const sl_bank* bank, double* norms, double* A, double* B
  * (sl_denoise and sl_forward_noalloc always take the general path). */
 sl_status sl_bank_path(const sl_bank* bank, int* path);
 
-/* The bank's precision mode (SL_PREC_FP32 or SL_PREC_TC_BF16). */
+/* The bank's precision mode (SL_PREC_FP32, SL_PREC_TC_BF16 or SL_PREC_TC_FP16). */
 sl_status sl_bank_precision(const sl_bank* bank, int* precision);
 
 /* Number of half-spectrum points Nh = N / n_last * (n_last/2 + 1), and N. */

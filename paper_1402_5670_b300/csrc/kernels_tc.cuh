@@ -14,6 +14,14 @@
 // A_lo B_hi + A_hi B_lo + A_hi B_hi (the A_lo B_lo term, ~2^-18 relative, is dropped),
 // which keeps each stage within about 1e-5 of FP32.
 //
+// FP16 operands (TC_OP_F16) carry 11 significant bits per part instead of BF16's 8,
+// so the split keeps about 22 bits, but FP16's range ends at 65504: before the split,
+// each warp scales its 16 x 8 block of operand B by a power of two 2^s that brings
+// the block's largest magnitude to [2^12, 2^13), and multiplies the FP32 products by
+// 2^-s (both exact). Values far below the block's largest lose relative precision in
+// the lo part (subnormal FP16), which bounds the error relative to the block maximum,
+// near 2^-22.
+//
 // Stage structure (decimation in time, in place). For a sub-length Ls = 8 Lr the data
 // of outer block o is x[o Ls + n'' + Lr n1] (n'' < Lr, digit n1 < 8). A stage takes
 // the length-8 DFT over n1 for every (o, n'', pencil), multiplies output digit k1 by
@@ -22,6 +30,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "kernels2d.cuh"
 
@@ -82,6 +91,51 @@ __device__ __forceinline__ void mma_bf16_16x8x16(float (&d)[4], const uint32_t (
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// (x0, x1) -> packed FP16 pairs hi = f16(x), lo = f16(x - hi); x0 in the low half.
+__device__ __forceinline__ void split_f16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void mma_f16_16x8x16(float (&d)[4], const uint32_t (&a)[4],
+                                                const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Operand type of the tensor-core stages (both operands of one product share it).
+enum TcOp { TC_OP_BF16 = 0, TC_OP_F16 = 1 };
+
+template <int OP>
+__device__ __forceinline__ void split_x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  if constexpr (OP == TC_OP_F16) split_f16x2(x0, x1, hi, lo);
+  else split_bf16x2(x0, x1, hi, lo);
+}
+
+template <int OP>
+__device__ __forceinline__ void mma_16x8x16(float (&d)[4], const uint32_t (&a)[4],
+                                            const uint32_t (&b)[2]) {
+  if constexpr (OP == TC_OP_F16) mma_f16_16x8x16(d, a, b);
+  else mma_bf16_16x8x16(d, a, b);
+}
+
+// Power-of-two scale of a warp's operand block for FP16 (header comment): returns
+// 2^s with s = 12 - floor(log2(max |v|)) clamped to [-126, 126], and 2^-s in *inv.
+// m is this lane's largest magnitude; every lane of the warp must call it.
+__device__ __forceinline__ float f16_block_scale(float m, float* inv) {
+  const uint32_t bits = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // m >= 0
+  const int e = (int)((bits >> 23) & 0xFF) - 127;
+  const int s = max(-126, min(126, 12 - e));
+  *inv = __uint_as_float((uint32_t)(127 - s) << 23);
+  return __uint_as_float((uint32_t)(127 + s) << 23);
+}
+
 // Entry (row, col) of the real 16 x 16 form of the length-8 DFT (header comment).
 template <int DIR>
 __device__ __forceinline__ float dft8_real_entry(int row, int col) {
@@ -94,7 +148,7 @@ __device__ __forceinline__ float dft8_real_entry(int row, int col) {
 }
 
 // A fragments (hi and lo) of the length-8 DFT matrix for this lane.
-template <int DIR>
+template <int DIR, int OP = TC_OP_BF16>
 struct Dft8Frag {
   uint32_t hi[4], lo[4];
   __device__ __forceinline__ void init(int lane) {
@@ -103,16 +157,16 @@ struct Dft8Frag {
     const int cols[4] = {2 * q, 2 * q, 2 * q + 8, 2 * q + 8};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      split_bf16x2(dft8_real_entry<DIR>(rows[i], cols[i]),
+      split_x2<OP>(dft8_real_entry<DIR>(rows[i], cols[i]),
                    dft8_real_entry<DIR>(rows[i], cols[i] + 1), hi[i], lo[i]);
   }
 };
 
 // One radix-8 stage over sub-length Ls on wk ([L][TC] complex, element (n, p) at
 // n * TC + p), in place; warps take n-tiles of 8 columns in turn.
-template <int L, int TC, int DIR>
+template <int L, int TC, int DIR, int OP>
 __device__ __forceinline__ void tc_radix8_stage(float2* wk, int Ls, const float2* wtab,
-                                                const Dft8Frag<DIR>& F, int warp, int lane) {
+                                                const Dft8Frag<DIR, OP>& F, int warp, int lane) {
   constexpr int NT = L * TC / 64;
   constexpr int NW = kTcThreads / 32;
   const int Lr = Ls >> 3;
@@ -123,21 +177,29 @@ __device__ __forceinline__ void tc_radix8_stage(float2* wk, int Ls, const float2
     const int c = nt * 8 + g;
     const int p = c % TC, rest = c / TC;
     const int base = ((rest / Lr) * Ls + rest % Lr) * TC + p;
-    const float2 x0 = wk[base + (2 * q) * dstride];
-    const float2 x1 = wk[base + (2 * q + 1) * dstride];
+    float2 x0 = wk[base + (2 * q) * dstride];
+    float2 x1 = wk[base + (2 * q + 1) * dstride];
+    float inv = 1.f;
+    if constexpr (OP == TC_OP_F16) {
+      const float sc = f16_block_scale(
+          fmaxf(fmaxf(fabsf(x0.x), fabsf(x0.y)), fmaxf(fabsf(x1.x), fabsf(x1.y))), &inv);
+      x0 = make_float2(x0.x * sc, x0.y * sc);
+      x1 = make_float2(x1.x * sc, x1.y * sc);
+    }
     uint32_t bh[2], bl[2];
-    split_bf16x2(x0.x, x1.x, bh[0], bl[0]);
-    split_bf16x2(x0.y, x1.y, bh[1], bl[1]);
+    split_x2<OP>(x0.x, x1.x, bh[0], bl[0]);
+    split_x2<OP>(x0.y, x1.y, bh[1], bl[1]);
     float d[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_bf16_16x8x16(d, F.lo, bh);
-    mma_bf16_16x8x16(d, F.hi, bl);
-    mma_bf16_16x8x16(d, F.hi, bh);
+    mma_16x8x16<OP>(d, F.lo, bh);
+    mma_16x8x16<OP>(d, F.hi, bl);
+    mma_16x8x16<OP>(d, F.hi, bh);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int c2 = nt * 8 + 2 * q + e;
       const int p2 = c2 % TC, rest2 = c2 / TC;
       const int nlo = rest2 % Lr;
       float2 y = make_float2(d[e], d[2 + e]);
+      if constexpr (OP == TC_OP_F16) y = make_float2(y.x * inv, y.y * inv);
       if (Lr > 1 && g != 0) y = ctw<DIR>(y, wtab[nlo * g * tscale]);
       wk[((rest2 / Lr) * Ls + nlo + g * Lr) * TC + p2] = y;
     }
@@ -146,8 +208,9 @@ __device__ __forceinline__ void tc_radix8_stage(float2* wk, int Ls, const float2
 
 // The whole DFT of the tile in wk (in place, digit-reversed output), CTA-wide.
 // Starts and ends with a barrier.
-template <int L, int TC, int DIR>
-__device__ __forceinline__ void tc_dft_tile(float2* wk, const float2* wtab, const Dft8Frag<DIR>& F) {
+template <int L, int TC, int DIR, int OP>
+__device__ __forceinline__ void tc_dft_tile(float2* wk, const float2* wtab,
+                                            const Dft8Frag<DIR, OP>& F) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int r = TcRadix<L>::r;
   int Ls = L;
@@ -171,7 +234,7 @@ __device__ __forceinline__ void tc_dft_tile(float2* wk, const float2* wtab, cons
   }
 #pragma unroll 1
   for (; Ls >= 8; Ls >>= 3) {
-    tc_radix8_stage<L, TC, DIR>(wk, Ls, wtab, F, warp, lane);
+    tc_radix8_stage<L, TC, DIR, OP>(wk, Ls, wtab, F, warp, lane);
     __syncthreads();
   }
 }
@@ -185,7 +248,7 @@ __device__ __forceinline__ void tc_load_twiddles(float2* wtab) {
 // Forward filter pass on the tensor cores: the contract of k_col_fwd_pipe (item i is
 // (tile i / nfilt, filter j0 + i % nfilt); out[s] = IFFT_0(in * psi[j0 + s])), with the
 // product formed and transformed in place in the item's shared-memory stage.
-template <int L>
+template <int L, int OP>
 __global__ void __launch_bounds__(kTcThreads) k_col_fwd_tc(ColArgs p) {
   constexpr int TC = col_tile_of(L), T = kTcThreads;
   constexpr int TILE = L * TC;
@@ -195,7 +258,7 @@ __global__ void __launch_bounds__(kTcThreads) k_col_fwd_tc(ColArgs p) {
   float2* wtab = reinterpret_cast<float2*>(ps + 2 * TILE);
   const int tid = threadIdx.x;
   const int nitems = (int)(p.Nhp / TILE) * p.nfilt;
-  Dft8Frag<1> F;
+  Dft8Frag<1, OP> F;
   F.init(tid & 31);
   tc_load_twiddles<L>(wtab);
 
@@ -219,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads) k_col_fwd_tc(ColArgs p) {
     cp_async_wait<1>();
     __syncthreads();
     for (int e = tid; e < TILE; e += T) wk[e] = cscale(wk[e], pk[e]);
-    tc_dft_tile<L, TC, 1>(wk, wtab, F);
+    tc_dft_tile<L, TC, 1, OP>(wk, wtab, F);
     const int tile = item / p.nfilt, s = item % p.nfilt;
     float2* o = p.out + (int64_t)s * p.Nhp + (int64_t)tile * TILE;
     for (int e = tid; e < TILE; e += T) o[e] = wk[tc_pos<L>(e / TC) * TC + e % TC];
@@ -232,7 +295,7 @@ __global__ void __launch_bounds__(kTcThreads) k_col_fwd_tc(ColArgs p) {
 // Inverse accumulation on the tensor cores: the contract of k_col_inv_pipe (item i is
 // (tile i % ntiles, split i / ntiles); out[part0 + split] = sum over the split's
 // filters of psi_j * FFT_0(in[j - j0])), one (item, filter) load per stage.
-template <int L>
+template <int L, int OP>
 __global__ void __launch_bounds__(kTcThreads) k_col_inv_tc(ColArgs p) {
   constexpr int TC = col_tile_of(L), T = kTcThreads;
   constexpr int TILE = L * TC, PER = TILE / T;
@@ -245,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads) k_col_inv_tc(ColArgs p) {
   const int ntiles = (int)(p.Nhp / TILE);
   const int nsplit = (p.nfilt + p.fps - 1) / p.fps;
   const int nitems = ntiles * nsplit;
-  Dft8Frag<-1> F;
+  Dft8Frag<-1, OP> F;
   F.init(tid & 31);
   tc_load_twiddles<L>(wtab);
 
@@ -282,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads) k_col_inv_tc(ColArgs p) {
     float2* wk = zs + stage * TILE;
     const float* pk = ps + stage * TILE;
     cp_async_wait<1>();
-    tc_dft_tile<L, TC, -1>(wk, wtab, F);
+    tc_dft_tile<L, TC, -1, OP>(wk, wtab, F);
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int e = tid + T * i;

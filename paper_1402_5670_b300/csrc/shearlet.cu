@@ -316,33 +316,46 @@ static cudaError_t launch_col_fwd_pipe(int L, int nitems, cudaStream_t st, const
 }
 
 // Tensor-core (split BF16) pencil passes, persistent like the FP32 pipelines.
-template <int L>
+template <int L, int OP>
 static cudaError_t launch_col_tc_t(bool fwd, int nitems, cudaStream_t st, const ColArgs& a) {
   constexpr int smem = sl::dev::tc_col_smem_bytes<L>();
   constexpr int T = sl::dev::kTcThreads;
+  constexpr bool f16 = OP == sl::dev::TC_OP_F16;
   if (fwd) {
-    auto k = sl::dev::k_col_fwd_tc<L>;
+    auto k = sl::dev::k_col_fwd_tc<L, OP>;
     cudaError_t e = ensure_smem(k, smem);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(nitems, persistent_grid(k, T, smem, 3000 + L));
-    return timed_launch("col_fwd_filter_tc", st, [&]() { k<<<grid, T, smem, st>>>(a); });
+    const int grid = std::min(nitems, persistent_grid(k, T, smem, 3000 + 100 * OP + L));
+    return timed_launch(f16 ? "col_fwd_filter_tc_f16" : "col_fwd_filter_tc", st,
+                        [&]() { k<<<grid, T, smem, st>>>(a); });
   }
-  auto k = sl::dev::k_col_inv_tc<L>;
+  auto k = sl::dev::k_col_inv_tc<L, OP>;
   cudaError_t e = ensure_smem(k, smem);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(nitems, persistent_grid(k, T, smem, 4000 + L));
-  return timed_launch("col_inv_accumulate_tc", st, [&]() { k<<<grid, T, smem, st>>>(a); });
+  const int grid = std::min(nitems, persistent_grid(k, T, smem, 4000 + 100 * OP + L));
+  return timed_launch(f16 ? "col_inv_accumulate_tc_f16" : "col_inv_accumulate_tc", st,
+                      [&]() { k<<<grid, T, smem, st>>>(a); });
 }
 
-static cudaError_t launch_col_tc(int L, bool fwd, int nitems, cudaStream_t st, const ColArgs& a) {
+template <int OP>
+static cudaError_t launch_col_tc_op(int L, bool fwd, int nitems, cudaStream_t st,
+                                    const ColArgs& a) {
   switch (L) {
-    case 64: return launch_col_tc_t<64>(fwd, nitems, st, a);
-    case 128: return launch_col_tc_t<128>(fwd, nitems, st, a);
-    case 256: return launch_col_tc_t<256>(fwd, nitems, st, a);
-    case 512: return launch_col_tc_t<512>(fwd, nitems, st, a);
-    case 1024: return launch_col_tc_t<1024>(fwd, nitems, st, a);
+    case 64: return launch_col_tc_t<64, OP>(fwd, nitems, st, a);
+    case 128: return launch_col_tc_t<128, OP>(fwd, nitems, st, a);
+    case 256: return launch_col_tc_t<256, OP>(fwd, nitems, st, a);
+    case 512: return launch_col_tc_t<512, OP>(fwd, nitems, st, a);
+    case 1024: return launch_col_tc_t<1024, OP>(fwd, nitems, st, a);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// prec: SL_PREC_TC_BF16 or SL_PREC_TC_FP16
+static cudaError_t launch_col_tc(int L, int prec, bool fwd, int nitems, cudaStream_t st,
+                                 const ColArgs& a) {
+  return prec == SL_PREC_TC_FP16
+             ? launch_col_tc_op<sl::dev::TC_OP_F16>(L, fwd, nitems, st, a)
+             : launch_col_tc_op<sl::dev::TC_OP_BF16>(L, fwd, nitems, st, a);
 }
 
 // Row passes: PAIRS row pairs per CTA. Launches over many filters use the wide
@@ -524,7 +537,7 @@ struct sl_bank {
   int ngroups = 1;
   int S = 1;        // partials per group
   int fps = 1;      // filters per partial
-  int prec = 0;     // SL_PREC_FP32 or SL_PREC_TC_BF16 (pencil passes on tensor cores)
+  int prec = 0;     // SL_PREC_FP32, or SL_PREC_TC_BF16 / _FP16 (pencil passes on tensor cores)
   float* psi = nullptr;       // [R][Nhp] tile-major
   double* invPsi = nullptr;   // [Nhp] tile-major
   float2* xhat = nullptr;     // [Nhp] spectrum of the signal
@@ -670,7 +683,8 @@ sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales, cons
   const int path = opt ? opt->path : SL_PATH_AUTO;
   if (path < SL_PATH_AUTO || path > SL_PATH_CLUSTER) return fail(SL_EINVAL, "unknown path");
   const int prec = opt ? opt->precision : SL_PREC_FP32;
-  if (prec != SL_PREC_FP32 && prec != SL_PREC_TC_BF16) return fail(SL_EINVAL, "unknown precision");
+  if (prec != SL_PREC_FP32 && prec != SL_PREC_TC_BF16 && prec != SL_PREC_TC_FP16)
+    return fail(SL_EINVAL, "unknown precision");
   if (ndim != 2 && ndim != 3) return fail(SL_EINVAL, "ndim must be 2 or 3");
   if (!dims || !shearLevels) return fail(SL_EINVAL, "dims or shearLevels is NULL");
   if (nScales < 1 || nScales > 8) return fail(SL_EINVAL, "nScales must be in [1, 8]");
@@ -695,7 +709,7 @@ sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales, cons
     if (dims[1] > 128 || dims[2] > 128)
       return fail(SL_ENOTSUP, "3D: axes 1 and 2 must be at most 128 (one plane per CTA)");
   }
-  if (prec == SL_PREC_TC_BF16) {
+  if (prec != SL_PREC_FP32) {
     if (path == SL_PATH_CLUSTER)
       return fail(SL_ENOTSUP, "tensor-core precision runs on the general path only");
     if (!is_pow2(dims[0]) || dims[0] < 64)
@@ -958,7 +972,7 @@ struct Plan {
   int G, ngroups, S, fps;
   const float* psi;   // tile-major [R][Nhp], or natural [R][Nh] when psi_natural
   int psi_natural;
-  int prec;           // 1: pencil passes of the filter loops on the tensor cores
+  int prec;           // != 0: pencil passes of the filter loops on the tensor cores
   const double* invPsi;
   float2* xhat;       // [Nhp]
   float2* scratch;    // [G][Nhp]
@@ -1075,7 +1089,7 @@ static sl_status fwd_filter_pass(const Plan& P, int j0, int nf, cudaStream_t st)
   ca.nfilt = nf;
   g_next_bytes = 4.0 * (double)P.Nh * nf;  // filters read
   if (P.prec && !P.psi_natural)
-    return launched(launch_col_tc((int)P.spec->dims[0], true, P.ntiles * nf, st, ca),
+    return launched(launch_col_tc((int)P.spec->dims[0], P.prec, true, P.ntiles * nf, st, ca),
                     "col_fwd_filter_tc");
   if (!P.psi_natural)
     return launched(launch_col_fwd_pipe((int)P.spec->dims[0], P.ntiles * nf, st, ca),
@@ -1099,7 +1113,7 @@ static sl_status inv_acc_pass(const Plan& P, int g_idx, int j0, int nf, cudaStre
   const int splits = (nf + P.fps - 1) / P.fps;
   g_next_bytes = 4.0 * (double)P.Nh * nf;  // filters read
   if (P.prec)
-    return launched(launch_col_tc((int)P.spec->dims[0], false, P.ntiles * splits, st, ca),
+    return launched(launch_col_tc((int)P.spec->dims[0], P.prec, false, P.ntiles * splits, st, ca),
                     "col_inv_accumulate_tc");
   return launched(launch_col_inv_pipe((int)P.spec->dims[0], P.ntiles * splits, st, ca),
                   "col_inv_accumulate");

@@ -147,7 +147,7 @@ class sl_options(ctypes.Structure):
                 ("reserved", ctypes.c_int * 6)]
 
 
-PRECISIONS = {"fp32": 0, "tc_bf16": 1}
+PRECISIONS = {"fp32": 0, "tc_bf16": 1, "tc_fp16": 2}
 
 
 class sl_filters(ctypes.Structure):

@@ -1,11 +1,13 @@
-"""Mixed-precision mode: the pencil passes of the per-filter loops as BF16 tensor-core
-DFT stages (split hi + lo operands, FP32 accumulation).
+"""Mixed-precision modes: the pencil passes of the per-filter loops as BF16 or FP16
+tensor-core DFT stages (split hi + lo operands, FP32 accumulation; FP16 operand blocks
+scaled by a power of two into range).
 
 Bar: 1e-3 relative to the FP64 oracle (max-abs error over max-abs reference), the
-tolerance stated for the BF16 tensor-core path; the split operands keep the measured
-error near 1e-5, which the tighter asserts below pin down so that a regression to
-single-term BF16 (about 4e-3) fails. The FP32 mode of the same bank shape is the
-comparison.
+tolerance stated for the BF16 tensor-core path. The split operands keep the measured
+BF16 error near 1e-5 (up to 1.4e-5 at 1024 x 128), which the tighter asserts pin down
+so that a regression to single-term BF16 (about 4e-3) fails. The FP16 split carries
+about 22 bits: measured 3e-7 to 7e-7, the FP32 mode's level, pinned at 2e-6 so that
+a silent fall-back to BF16 operands (1e-5) or a lost block scale fails.
 """
 import numpy as np
 import pytest
@@ -16,7 +18,9 @@ from paper_1402_5670_b300 import synth
 from tests.conftest import oracle_system
 
 TOL_TC = 1e-3    # stated bound of the BF16 tensor-core path
-TIGHT = 1e-4     # what the split-precision stages actually keep
+TIGHT = 1e-4     # what the BF16 split-precision stages actually keep
+TIGHT_F16 = 2e-6  # what the FP16 split keeps (FP32 level)
+MODES = [("tc_bf16", TIGHT), ("tc_fp16", TIGHT_F16)]
 
 
 def rel(a, b):
@@ -25,14 +29,15 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+@pytest.mark.parametrize("mode", ["tc_bf16", "tc_fp16"])
 @pytest.mark.parametrize("dims,kw,err", [
     ((64, 64), {"path": "cluster"}, "SL_ENOTSUP"),   # general path only
     ((384, 64), {}, "SL_ENOTSUP"),                  # n0 must be a power of two
     ((32, 64), {}, "SL_ENOTSUP"),                   # n0 >= 64
 ])
-def test_tc_mode_rejects_unsupported_banks(dims, kw, err):
+def test_tc_mode_rejects_unsupported_banks(dims, kw, err, mode):
     with pytest.raises(S.ShearletError) as ei:
-        S.sl_build_filters_ex(dims, 2, (1, 1), False, -1, precision="tc_bf16", **kw)
+        S.sl_build_filters_ex(dims, 2, (1, 1), False, -1, precision=mode, **kw)
     assert err in str(ei.value)
 
 
@@ -47,9 +52,10 @@ def test_unknown_precision_is_rejected():
     assert S.STATUS[st] == "SL_EINVAL"
 
 
-def test_host_bank_reports_its_precision():
-    b = S.Bank((64, 64), 2, (1, 1), device=-1, precision="tc_bf16")
-    assert b.precision == "tc_bf16"
+@pytest.mark.parametrize("mode", ["fp32", "tc_bf16", "tc_fp16"])
+def test_host_bank_reports_its_precision(mode):
+    b = S.Bank((64, 64), 2, (1, 1), device=-1, precision=mode)
+    assert b.precision == mode
     b.close()
 
 
@@ -82,31 +88,50 @@ def cuda(a):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("mode,tight", MODES, ids=[m for m, _ in MODES])
 @pytest.mark.parametrize("case", CASES, ids=str)
-def test_tc_mode_matches_oracle(cuda_ready, case):
+def test_tc_mode_matches_oracle(cuda_ready, case, mode, tight):
     dims, J, sl = case
-    b = S.Bank(dims, J, sl, device=0, precision="tc_bf16")
-    assert b.precision == "tc_bf16"
+    b = S.Bank(dims, J, sl, device=0, precision=mode)
+    assert b.precision == mode
     s = oracle_system(dims, J, sl)
     x = signal(dims, 1)
     C = b.forward(cuda(x))
     ref = O.forward(x.astype(np.float64), s)
     e_fwd = rel(C.cpu().numpy(), ref)
-    assert e_fwd < TOL_TC and e_fwd < TIGHT, e_fwd
+    assert e_fwd < TOL_TC and e_fwd < tight, e_fwd
     Cf = C.cpu().numpy().astype(np.float64)
     xi = b.inverse(C).cpu().numpy()
-    assert rel(xi, O.inverse(Cf, s)) < TIGHT
-    assert rel(xi, x) < TIGHT
+    assert rel(xi, O.inverse(Cf, s)) < tight
+    assert rel(xi, x) < tight
     Cr = synth.gaussian_field((b.R,) + tuple(dims), 2)
-    assert rel(b.adjoint(cuda(Cr)).cpu().numpy(), O.adjoint(Cr.astype(np.float64), s)) < TIGHT
+    assert rel(b.adjoint(cuda(Cr)).cpu().numpy(), O.adjoint(Cr.astype(np.float64), s)) < tight
     b.close()
 
 
 @pytest.mark.gpu
-def test_tc_mode_denoise_quality(cuda_ready):
+def test_fp16_mode_handles_large_and_tiny_magnitudes(cuda_ready):
+    """The block scale keeps FP16 operands in range whatever the data's magnitude:
+    the same image times 2^40 and times 2^-40 gives the same relative error (the
+    spectra of the unscaled image already exceed FP16's 65504)."""
+    dims, J, sl = (256, 256), 3, (1, 1, 2)
+    b = S.Bank(dims, J, sl, device=0, precision="tc_fp16")
+    s = oracle_system(dims, J, sl)
+    x = signal(dims, 3)
+    ref = O.forward(x.astype(np.float64), s)
+    for f in (1.0, 2.0 ** 40, 2.0 ** -40):
+        C = b.forward(cuda(x * f)).cpu().numpy().astype(np.float64) / f
+        assert np.all(np.isfinite(C))
+        assert rel(C, ref) < TIGHT_F16, f
+    b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["tc_bf16", "tc_fp16"])
+def test_tc_mode_denoise_quality(cuda_ready, mode):
     """Same PSNR as the FP64 denoiser to 0.01 dB at 512^2, sigma = 20."""
     dims, J, sl = (512, 512), 4, (1, 1, 2, 2)
-    b = S.Bank(dims, J, sl, device=0, precision="tc_bf16")
+    b = S.Bank(dims, J, sl, device=0, precision=mode)
     s = oracle_system(dims, J, sl)
     K = [2.5, 2.5, 2.5, 3.8]
     clean = synth.piecewise_smooth_image(dims, 5)
@@ -123,8 +148,9 @@ def test_tc_and_fp32_modes_agree_in_a_batch(cuda_ready):
     dims = (256, 256)
     bt = S.Bank(dims, 2, (1, 1), device=0, precision="tc_bf16")
     bf = S.Bank(dims, 2, (1, 1), device=0)
+    bh = S.Bank(dims, 2, (1, 1), device=0, precision="tc_fp16")
     xs = [cuda(signal(dims, 20 + i)) for i in range(4)]
-    banks = [bt, bf, bt, bf]
+    banks = [bt, bf, bh, bf]
     cs = [torch.empty((b.R,) + dims, device="cuda") for b in banks]
     B = S.Batch(banks, branches=2)
     B.forward(xs, cs)
@@ -132,6 +158,8 @@ def test_tc_and_fp32_modes_agree_in_a_batch(cuda_ready):
     for b, x, c in zip(banks, xs, cs):
         assert torch.equal(c, b.forward(x))
     assert rel(cs[0].cpu().numpy(), bf.forward(xs[0]).cpu().numpy()) < TIGHT
+    assert rel(cs[2].cpu().numpy(), bf.forward(xs[2]).cpu().numpy()) < TIGHT_F16
     B.close()
     bt.close()
     bf.close()
+    bh.close()
