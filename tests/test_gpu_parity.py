@@ -249,6 +249,28 @@ def test_full_size_3d_128():
     assert rel(xi, x) < TOL
 
 
+def test_full_size_2d_1024():
+    """1024^2 (the largest 2D grid), four scales, levels (1,1,2,2): R = 49. Sampled
+    subbands against the oracle's filters applied by FP64 FFTs, plus perfect
+    reconstruction and the inverse of the GPU's own coefficients."""
+    dims, J, sl = (1024, 1024), 4, (1, 1, 2, 2)
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    assert b.R == 49
+    x = signal(dims, 15)
+    C = b.forward(cuda(x))
+    X = np.fft.fft2(x.astype(np.float64))
+    scale = None
+    for j in (0, 1, 12, 25, 33, 48):
+        ref = np.real(np.fft.ifft2(X * s.psi_hat(j)))
+        got = C[j].cpu().numpy()
+        scale = np.max(np.abs(ref)) if j == 0 else scale
+        assert np.max(np.abs(got - ref)) / scale < TOL, j
+    xi = b.inverse(C).cpu().numpy()
+    assert rel(xi, x) < TOL
+    del C
+
+
 def test_error_stats_kernel_matches_numpy():
     """The FP64-accumulating GPU reduction (max and L2 errors, PSNR of eq. PSNR)."""
     from paper_1402_5670_b300.shearlet import sl_error_stats
