@@ -1234,6 +1234,12 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
   a.inv_s = M->inv_s;
   a.geo = M->geo;
   a.R = M->R;
+  // The BF16 weight tiles are repacked when the parameters changed, on another
+  // stream, and always inside a stream capture (a replayed graph must not depend on
+  // what was packed when it was captured).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return mfail(SL_ECUDA, "cudaStreamIsCapturing");
+  const bool repack = !M->tc_packed || M->pack_stream != st || cap != cudaStreamCaptureStatusNone;
   if (M->engine == SL_MLP_TCGEN05) {
     // the grid keeps every SM's CTAs within its 512 TMEM columns: no allocation waits
     if (M->ndim == 2) {
@@ -1241,7 +1247,7 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
       cudaFuncSetAttribute(k_mlp_apply_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       cudaFuncSetAttribute(k_mlp_apply_tc<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       auto* wt = reinterpret_cast<TcWeights<2>*>(M->tc_pack);
-      if (!M->tc_packed || M->pack_stream != st)
+      if (repack)
         k_mlp_pack_tc<2><<<(tc_pack_elems<2>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
       k_mlp_apply_tc<2><<<apply_tc_grid<2>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
     } else {
@@ -1249,7 +1255,7 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
       cudaFuncSetAttribute(k_mlp_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       cudaFuncSetAttribute(k_mlp_apply_tc<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       auto* wt = reinterpret_cast<TcWeights<3>*>(M->tc_pack);
-      if (!M->tc_packed || M->pack_stream != st)
+      if (repack)
         k_mlp_pack_tc<3><<<(tc_pack_elems<3>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
       k_mlp_apply_tc<3><<<apply_tc_grid<3>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
     }
@@ -1267,8 +1273,8 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_mlp_apply: ") + cudaGetErrorString(e));
-  if (M->engine == SL_MLP_TCGEN05) {
-    M->tc_packed = true;
+  if (M->engine == SL_MLP_TCGEN05 && repack) {
+    M->tc_packed = cap == cudaStreamCaptureStatusNone;  // a capture packs nothing yet
     M->pack_stream = st;
   }
   return SL_OK;

@@ -214,6 +214,33 @@ def test_gpu_apply_engines_agree_at_full_size():
 
 
 @pytest.mark.gpu
+def test_apply_in_a_graph_follows_parameter_updates():
+    """A CUDA graph that captured sl_mlp_apply repacks the tcgen05 weight tiles at
+    every replay, so a parameter update between replays is seen, bit for bit as an
+    eager call with the new parameters."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dims, J, sl = (64, 64), 2, (1, 1)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 5)
+    out = torch.empty_like(Cn)
+    mlp.apply(Cn, 20.0, out=out)  # packs on the current stream first
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mlp.apply(Cn, 20.0, out=out)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, mlp.apply(Cn, 20.0))
+    mlp.set_params(0.5 * flat)
+    g.replay()
+    torch.cuda.synchronize()
+    want = mlp.apply(Cn, 20.0)
+    mlp.check()
+    assert torch.equal(out, want)
+    assert not torch.equal(want[1:], Cn[1:])
+
+
+@pytest.mark.gpu
 def test_learned_shrinkage_beats_hard_thresholding():
     """Trained on the GPU from transform-generated pairs, the learned gain must denoise
     held-out synthetic images better (PSNR) than the paper's hard threshold at every
