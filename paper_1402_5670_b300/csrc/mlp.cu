@@ -657,13 +657,21 @@ __global__ void __launch_bounds__(TC_THREADS)
 // Persistent grid: every SM holds as many CTAs as its registers, shared memory and
 // tensor memory (TC_TMEM_COLS of 512 columns each) allow. (The occupancy calculator
 // is not used: for this kernel it reports one CTA per SM, below what runs.)
+static int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
 template <int NDIM>
 static int apply_tc_grid() {
-  static int grid = 0;
-  if (!grid) {
-    int dev = 0, sms = 148, smem_sm = 228 * 1024, regs_sm = 65536;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static int grid[64] = {0};  // per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!grid[dev]) {
+    int smem_sm = 228 * 1024, regs_sm = 65536;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     cudaFuncAttributes fa{};
@@ -671,9 +679,9 @@ static int apply_tc_grid() {
     const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8) * TC_THREADS;
     const int smem = (int)sizeof(TcApplySmem<NDIM>) + 1024;  // + the per-CTA reserve
     int per_sm = std::min({512 / TC_TMEM_COLS, smem_sm / smem, regs_sm / regs});
-    grid = std::max(1, per_sm) * sms;
+    grid[dev] = std::max(1, per_sm) * sm_count();
   }
-  return grid;
+  return grid[dev];
 }
 
 // Training: forward and backward on a sample; gradients accumulate into a.grad.
@@ -1173,7 +1181,7 @@ static sl_status train_launch(sl_mlp* M, const float* noisy, const float* clean,
   a.geo = M->geo;
   a.R = M->R;
   const int tiles = n / ROWS;
-  const int grid = std::min(tiles, 4 * 148);
+  const int grid = std::min(tiles, 4 * sm_count());
   if (M->ndim == 2) {
     const size_t sm = train_smem<2>();
     cudaFuncSetAttribute(k_mlp_train<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1260,7 +1268,7 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
       k_mlp_apply_tc<3><<<apply_tc_grid<3>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
     }
   } else {
-    const int grid = 4 * 148;
+    const int grid = 4 * sm_count();
     if (M->ndim == 2) {
       const size_t sm = apply_smem<2>();
       cudaFuncSetAttribute(k_mlp_apply<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
