@@ -29,7 +29,8 @@ What it computes, step by step in the paper's order and notation:
 
 Every filter is built in the SPATIAL domain with explicit upsampling, convolution,
 shearing and downsampling of finite arrays, then folded periodically onto the
-N-grid and transformed with numpy's FFT (a library primitive). Readings taken where
+N-grid and transformed with the oracle's own DFT (oracle/dft_oracle.py: the direct
+sum on tiny lengths, decimation in time by 2 (and once by 3) beyond). Readings taken where
 the paper is silent or ambiguous are marked "Reading:" below; each is listed in the
 design notes.
 
@@ -46,6 +47,8 @@ from dataclasses import dataclass, field
 from typing import Callable, Iterator, List, Optional, Sequence, Tuple, Union
 
 import numpy as np
+
+from oracle import dft_oracle as _dft
 
 # --------------------------------------------------------------------------------
 # Finite arrays. Every filter here has odd extent on every axis with the origin
@@ -265,7 +268,7 @@ def dft_real(a_folded: np.ndarray, l1: Optional[float] = None) -> np.ndarray:
     DFT is real; the (rounding-level) imaginary part is checked and dropped.
     ``l1`` is the l1 norm of the unfolded filter (it bounds |F| and the rounding
     error of the fold); by default that of the folded array."""
-    F = np.fft.fftn(a_folded)
+    F = _dft.fftn(a_folded)
     scale = float(np.sum(np.abs(a_folded))) if l1 is None else float(l1)
     assert float(np.max(np.abs(F.imag))) <= 1e-12 * scale, "filter spectrum not real"
     return np.ascontiguousarray(F.real)
@@ -627,9 +630,9 @@ def forward_iter(x: np.ndarray, sysm: ShearletSystem) -> Iterator[Tuple[int, np.
     (eq. convolution, Def. digitSH_alpha); the algorithm box conjugates the signal
     spectrum instead, which for the real filters here would reverse the coefficient
     index (reading: follow the definition)."""
-    X = np.fft.fftn(np.asarray(x, dtype=np.float64))
+    X = _dft.fftn(np.asarray(x, dtype=np.float64))
     for j in range(sysm.R):
-        yield j, np.real(np.fft.ifftn(X * np.conj(sysm.psi_hat(j))))
+        yield j, np.real(_dft.ifftn(X * np.conj(sysm.psi_hat(j))))
 
 
 def forward(x: np.ndarray, sysm: ShearletSystem) -> np.ndarray:
@@ -648,8 +651,8 @@ def adjoint(C: CoeffSource, sysm: ShearletSystem) -> np.ndarray:
     """SH* C = Re IFFT( sum_j FFT(C_j) psi_hat_j ): the adjoint of forward."""
     acc = np.zeros(sysm.dims, dtype=np.complex128)
     for j in range(sysm.R):
-        acc += np.fft.fftn(_coeff(C, j)) * sysm.psi_hat(j)
-    return np.real(np.fft.ifftn(acc))
+        acc += _dft.fftn(_coeff(C, j)) * sysm.psi_hat(j)
+    return np.real(_dft.ifftn(acc))
 
 
 def inverse(C: CoeffSource, sysm: ShearletSystem) -> np.ndarray:
@@ -657,8 +660,8 @@ def inverse(C: CoeffSource, sysm: ShearletSystem) -> np.ndarray:
     x = Re IFFT( sum_j FFT(C_j) gamma_hat_j ), gamma_hat_j = psi_hat_j / Psi (eq. dual_filter)."""
     acc = np.zeros(sysm.dims, dtype=np.complex128)
     for j in range(sysm.R):
-        acc += np.fft.fftn(_coeff(C, j)) * (sysm.psi_hat(j) / sysm.Psi)
-    return np.real(np.fft.ifftn(acc))
+        acc += _dft.fftn(_coeff(C, j)) * (sysm.psi_hat(j) / sysm.Psi)
+    return np.real(_dft.ifftn(acc))
 
 
 def thresholds(sysm: ShearletSystem, sigma: float, K: Sequence[float]) -> np.ndarray:
@@ -695,15 +698,15 @@ def denoise(x: np.ndarray, sysm: ShearletSystem, sigma: float, K: Sequence[float
             dtype=np.float64) -> np.ndarray:
     """f_denoised = T^-1 T_delta T f_noisy (Sec. 5.3), streaming over filters."""
     dl = thresholds(sysm, sigma, K)
-    X = np.fft.fftn(np.asarray(x, dtype=np.float64))
+    X = _dft.fftn(np.asarray(x, dtype=np.float64))
     acc = np.zeros(sysm.dims, dtype=np.complex128)
     for j in range(sysm.R):
         F = sysm.psi_hat(j)
-        C = np.real(np.fft.ifftn(X * np.conj(F)))
+        C = np.real(_dft.ifftn(X * np.conj(F)))
         if sysm.meta[j].scale >= 0:
             C = hard_threshold(C, dl[j], dtype)
-        acc += np.fft.fftn(C) * (F / sysm.Psi)
-    return np.real(np.fft.ifftn(acc))
+        acc += _dft.fftn(C) * (F / sysm.Psi)
+    return np.real(_dft.ifftn(acc))
 
 
 def inpaint_ratio(delta_init: float, delta_min: float, iterations: int) -> float:

@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import dft_oracle as D
 from oracle import shearlet_oracle as O
 from paper_1402_5670_b300 import synth
 from tests.conftest import oracle_system, read_golden
@@ -334,6 +335,156 @@ def test_denoising_improves_psnr():
     y = synth.add_noise(x, 20.0, 4).astype(np.float64)
     z = O.denoise(y, s, 20.0, [2.5, 3.8])
     assert O.psnr(x, z) > O.psnr(x, y) + 4.0
+
+
+# ------------------------------------------------------- the oracle's own DFT ---
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 12, 16])
+def test_direct_dft_closed_forms(n):
+    """The defining sum on closed forms: the DFT of the unit impulse at a is
+    exp(-2 pi i a k / n), the DFT of exp(+2 pi i m t / n) is n at k = m and 0 elsewhere
+    (fixes the sign convention), and the inverse sum brings the impulse back."""
+    k = np.arange(n)
+    for a in range(n):
+        e = np.zeros(n)
+        e[a] = 1.0
+        want = np.exp(-2j * np.pi * a * k / n)
+        assert np.max(np.abs(D.dft_direct(e) - want)) <= 1e-14 * n
+        assert np.max(np.abs(D.dft_direct(want, sign=+1) / n - e)) <= 1e-14 * n
+    for m in range(n):
+        x = np.exp(2j * np.pi * m * k / n)
+        want = np.zeros(n)
+        want[m] = n
+        assert np.max(np.abs(D.dft_direct(x) - want)) <= 1e-13 * n
+
+
+@pytest.mark.parametrize("n", [9, 16, 24, 64, 96, 128, 192, 256, 384, 512, 1024])
+def test_fft_equals_direct_dft(n):
+    """The recursive FFT (radix 2, one radix-3 step for 3 * 2^k) equals the direct sum
+    to 1e-13 relative, both directions, on seeded complex data."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for sign in (-1, 1):
+        want = D.dft_direct(x, sign=sign)
+        assert np.max(np.abs(D.fft(x, sign=sign) - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_fftn_is_separable_and_inverts():
+    """fftn applies the 1D DFT along each axis (checked axis by axis against the direct
+    sum on a 12 x 8 x 6 grid), and ifftn(fftn(x)) = x to 1e-14."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((12, 8, 6))
+    want = D.dft_direct(D.dft_direct(D.dft_direct(x, 0), 1), 2)
+    got = D.fftn(x)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+    assert np.max(np.abs(D.ifftn(got) - x)) <= 1e-14 * np.max(np.abs(x)) * 10
+
+
+def test_pin_catches_wrong_fft_twiddle(monkeypatch):
+    """Planted mistake: the inter-stage twiddle of the FFT with the wrong sign. The
+    FFT-versus-direct-sum pin must fail."""
+    orig = D._twiddle
+    monkeypatch.setattr(D, "_twiddle", lambda r, k1, n_len, sign: orig(r, k1, n_len, -sign))
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(64) + 1j * rng.standard_normal(64)
+    want = D.dft_direct(x)
+    assert np.max(np.abs(D.fft(x) - want)) > 1e-3 * np.max(np.abs(want))
+
+
+# ------------------------------------------------ filter norms and thresholds ---
+
+
+def _parseval_deviation(dims, J, sl):
+    """max_j | ||psi_j||_2^2 (the oracle's norm) / sum_n psi_j(n)^2 - 1 |, the sum taken
+    over the filter folded onto the grid in SPACE (Parseval's identity on Z_N): the
+    norm the thresholds use must be the l2 norm of the spatial filter."""
+    s = O.build_system(dims, J, sl)
+    dev = 0.0
+    for j in range(s.R):
+        e = float(np.sum(s.psi_spatial(j) ** 2))
+        dev = max(dev, abs(float(s.norms[j]) ** 2 / e - 1.0))
+    return dev
+
+
+def _white_noise_stats(sigma=3.0, draws=400, K=1.0):
+    """Monte Carlo over seeded Gaussian noise of std sigma on a 32x32 grid (J = 2,
+    levels (0, 1)). Returns (max_j |std(C_j) / (sigma ||psi_j||) - 1|, max_j>=1 |P(|C_j|
+    >= delta_j) - 2 (1 - Phi(K))|) with delta_j from the oracle's thresholds at K.
+    For white noise C_j(m) ~ N(0, sigma^2 sum_n psi_j(n)^2) exactly, so the threshold
+    K sigma ||psi_j||_2 of the hard-thresholding rule (Sec. 5.3) is exceeded with
+    the two-sided Gaussian tail probability."""
+    s = O.build_system((32, 32), 2, (0, 1))
+    rng = np.random.default_rng(np.random.PCG64(77))
+    dl = O.thresholds(s, sigma, [K, K])
+    var = np.zeros(s.R)
+    hit = np.zeros(s.R)
+    for _ in range(draws):
+        C = O.forward(sigma * rng.standard_normal((32, 32)), s)
+        var += (C ** 2).reshape(s.R, -1).mean(axis=1)
+        hit += (np.abs(C) >= dl[:, None, None]).reshape(s.R, -1).mean(axis=1)
+    std_dev = float(np.max(np.abs(np.sqrt(var / draws) / (sigma * s.norms) - 1.0)))
+    tail = math.erfc(K / math.sqrt(2.0))          # 2 (1 - Phi(K))
+    tail_dev = float(np.max(np.abs(hit[1:] / draws - tail)))
+    return std_dev, tail_dev
+
+
+@pytest.mark.parametrize("case", [((16, 16), 2, (0, 1)), ((24, 16), 1, (1,)),
+                                  ((8, 8, 8), 1, (1,))], ids=str)
+def test_norms_equal_spatial_l2_norm(case):
+    """||psi_j||_2 (the factor of the threshold delta_j = K sigma ||psi_j||_2) equals
+    the l2 norm of the filter in space, computed from the folded spatial filter
+    rather than from its spectrum (Parseval on Z_N)."""
+    assert _parseval_deviation(*case) <= 1e-12
+
+
+@pytest.mark.slow
+def test_norms_are_subband_noise_std_and_thresholds_hit_gaussian_tail():
+    """Sec. 5.3 thresholds subband j at K sigma ||psi_j||_2: the standard deviation of
+    the subband's response to white noise of std sigma. Monte Carlo (400 seeded
+    draws): the sample std matches sigma ||psi_j|| to 2% and |C_j| >= delta_j (K = 1)
+    occurs with probability erfc(1/sqrt 2) = 0.3173 to 0.015."""
+    std_dev, tail_dev = _white_noise_stats()
+    assert std_dev < 0.02, std_dev
+    assert tail_dev < 0.015, tail_dev
+
+
+def test_pin_catches_norm_without_grid_size(monkeypatch):
+    """Planted mistake: ||psi_j||^2 = sum_xi psi_hat^2 (no 1/N). Parseval must fail."""
+    orig = O._finish_system
+
+    def bad(sysm):
+        sysm = orig(sysm)
+        sysm.norms = sysm.norms * math.sqrt(sysm.N)
+        return sysm
+    monkeypatch.setattr(O, "_finish_system", bad)
+    assert _parseval_deviation((16, 16), 2, (0, 1)) > 0.5
+
+
+def test_pin_catches_norm_without_sqrt(monkeypatch):
+    """Planted mistake: the squared norm used as the norm. Parseval must fail."""
+    orig = O._finish_system
+
+    def bad(sysm):
+        sysm = orig(sysm)
+        sysm.norms = sysm.norms ** 2
+        return sysm
+    monkeypatch.setattr(O, "_finish_system", bad)
+    assert _parseval_deviation((16, 16), 2, (0, 1)) > 0.5
+
+
+@pytest.mark.slow
+def test_pin_catches_threshold_without_sigma(monkeypatch):
+    """Planted mistake: delta_j = K ||psi_j|| (sigma dropped). The tail pin must fail."""
+    def bad_thresholds(sysm, sigma, K):
+        d = np.zeros(sysm.R)
+        for j, m in enumerate(sysm.meta):
+            if m.scale >= 0:
+                d[j] = float(K[m.scale]) * float(sysm.norms[j])
+        return d
+    monkeypatch.setattr(O, "thresholds", bad_thresholds)
+    _, tail_dev = _white_noise_stats(draws=50)
+    assert tail_dev > 0.1
 
 
 # ------------------------------------------------- planted mistakes are caught ---
