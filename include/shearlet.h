@@ -147,6 +147,21 @@ sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales,
                                 const sl_options* opt, const sl_filters* filters,
                                 sl_bank** out);
 
+/*
+ * The separable stationary wavelet system on the same grid (the isotropic dictionary
+ * of the image decomposition, Sec. 5.5: "the stationary wavelet transform"), as a
+ * bank that every transform call of this header accepts. Filters, in this order:
+ * the lowpass h_J(xi_1) h_J(xi_2) (the shearlet system's lowpass), then for each scale
+ * j = 0..J-1 coarse to fine, with a = J - j and h_a, g_a the a trous filters of eq.
+ * lowhigh: g_a(xi_1) h_a(xi_2), h_a(xi_1) g_a(xi_2), g_a(xi_1) g_a(xi_2)
+ * (sl_bank_filter_meta: scale j, cone 1, 2, 3). R = 1 + 3 J. Normalised like a shearlet
+ * bank (max Psi = 1, 1/Psi in FP64), so sl_inverse is the dual-frame inverse.
+ *   ndim 2 only (SL_ENOTSUP for 3); dims and nScales as sl_build_filters; filters
+ *   may be NULL or give a user QMF lowpass (its fan member must be NULL).
+ */
+sl_status sl_build_wavelets(int ndim, const int64_t* dims, int nScales, int device,
+                            const sl_filters* filters, sl_bank** out);
+
 /* Release a bank and all library memory it holds. NULL is ignored. Call it with no
  * transform of this bank still running on the GPU. */
 void sl_free_filters(sl_bank* bank);
@@ -197,6 +212,52 @@ sl_status sl_adjoint(const sl_bank* bank, const float* coeffs, float* x, void* s
  * The division by Psi is done in FP64. sl_inverse(sl_forward(x)) = x up to rounding. */
 sl_status sl_inverse(const sl_bank* bank, const float* coeffs, float* x, void* stream);
 
+/* ------------------------------------------------------ filter ranges ---
+ * One transform split by filters, for running it on several GPUs (one rank each).
+ * The inverse of eq. reconstruction is a sum over j of FFT(C_j) psi_hat_j / Psi
+ * (Algorithm 2), so a rank that holds the coefficients of filters [j0, j1) turns them
+ * into one partial spectrum; the ranks add their partials (one reduction, e.g.
+ * ncclAllReduce or ncclReduce of 2 * n_points floats, sum), and one rank finishes
+ * with the division by Psi and the inverse FFT. The forward transform (Algorithm 1)
+ * needs X_hat = FFT(x) on every rank (one broadcast of 2 * n_points floats), after
+ * which each rank produces its own range. Every call here takes the general kernel
+ * path (whatever the bank's path) and the bank's precision mode; sharded and
+ * unsharded results agree to rounding (partials summed in another order).
+ * Spectrum buffers are DEVICE float arrays of 2 * n_points floats (complex
+ * interleaved) in the library's internal layout (a half spectrum cut into pencil
+ * tiles, padded); adding two of them elementwise adds the spectra, and nothing else
+ * about the layout may be assumed. 16-byte aligned like every other array.
+ */
+
+/* n_points: complex points in one spectrum buffer of this bank. */
+sl_status sl_spectrum_points(const sl_bank* bank, int64_t* n_points);
+
+/* X_hat = FFT(x), the first step of Algorithm 1: x DEVICE [dims] -> xhat (spectrum
+ * buffer). Errors as sl_forward. */
+sl_status sl_spectrum(const sl_bank* bank, const float* x, float* xhat, void* stream);
+
+/* C_j = Re IFFT(X_hat conj(psi_hat_j)) for j in [j0, j1) (Algorithm 1's loop over a
+ * filter range; eq. convolution): xhat a spectrum buffer from sl_spectrum (read only),
+ * coeffs DEVICE [j1 - j0][dims] (plane i holds filter j0 + i). Concatenating the
+ * ranges of all ranks gives exactly sl_forward's coefficients (same kernels).
+ * SL_EINVAL unless 0 <= j0 <= j1 <= R; an empty range does nothing (coeffs may then
+ * be NULL). */
+sl_status sl_forward_range(const sl_bank* bank, const float* xhat, int j0, int j1,
+                           float* coeffs, void* stream);
+
+/* partial = sum_{j in [j0, j1)} FFT(C_j) psi_hat_j (the inner sum of eq. reconstruction
+ * over one filter range): coeffs DEVICE [j1 - j0][dims] as sl_forward_range writes
+ * them (NULL allowed for an empty range); partial a spectrum buffer, overwritten
+ * (zeros for an empty range). */
+sl_status sl_inverse_partial(const sl_bank* bank, const float* coeffs, int j0, int j1,
+                             float* partial, void* stream);
+
+/* x = Re IFFT(summed / Psi) (dual = 1: the dual-frame inverse of eq. reconstruction,
+ * division in FP64) or Re IFFT(summed) (dual = 0: the adjoint), where summed is the
+ * sum of every range's partial (a spectrum buffer, read only); x DEVICE [dims]. */
+sl_status sl_inverse_finish(const sl_bank* bank, const float* summed, int dual, float* x,
+                            void* stream);
+
 /*
  * Hard thresholding in place (eq. hard_tresholding, Sec. 5.3): for every filter
  * j >= 1, C_j(m) = 0 unless |C_j(m)| >= K[scale(j)] * sigma * ||psi_j||_2. The lowpass
@@ -228,6 +289,32 @@ sl_status sl_denoise(const sl_bank* bank, const float* noisy, float* out, float 
  */
 sl_status sl_inpaint(const sl_bank* bank, const float* f_masked, const uint8_t* mask, float* out,
                      float delta_init, float delta_min, int iterations, void* stream);
+
+/*
+ * Image decomposition by iterative thresholding (Sec. 5.5, algorithm
+ * image_decomposition): f = f0 + f1 with f0 the curvilinear part, sparse in the
+ * shearlet bank `curv`, and f1 the isotropic part, sparse in the wavelet bank `iso`
+ * (sl_build_wavelets; same grid and device). f, f0, f1: DEVICE [dims]; f0 and f1 are
+ * outputs and must not alias f or each other. Starting from f0 = f1 = 0, each of the
+ * `iterations` steps does
+ *     f0 = T0^-1 Thr_delta T0 (f - f1)        (= the algorithm's f_res + f0)
+ *     f1 = T1^-1 Thr_delta T1 (f - f0)        (f0 already updated: see below)
+ * and then shrinks delta geometrically from delta_init to delta_min (as sl_inpaint).
+ * Thr_delta keeps coefficient C_j(m) of subband j >= 1 iff |C_j(m)| >= delta ||psi_j||_2
+ * (the denoising rule with K = 1, sigma = delta). The curvilinear part gets no lowpass
+ * (the shearlet lowpass subband is dropped) and the wavelet lowpass is kept, so the
+ * smooth content goes to f1. The residual is recomputed between the two updates (the
+ * block-coordinate order of the morphological component analysis the paper cites);
+ * the algorithm as printed computes it once per step, which makes content that both
+ * dictionaries represent enter both parts at once. Work per step: two elementwise
+ * passes and two fused denoising passes (one per bank). The bank `curv` keeps one
+ * [dims] float buffer (allocated on first use, shared with sl_inpaint).
+ * Errors: SL_EINVAL (banks of different grids or devices, aliasing, iterations < 1,
+ * non-positive or non-finite deltas), SL_ENOMEM, SL_ECUDA.
+ */
+sl_status sl_decompose(const sl_bank* curv, const sl_bank* iso, const float* f, float* f0,
+                       float* f1, float delta_init, float delta_min, int iterations,
+                       void* stream);
 
 /*
  * End-to-end round trip from HOST memory: copies x_host[dims] to the device,
@@ -326,8 +413,10 @@ sl_status sl_inverse_batch(const sl_bank* const* banks, int n, const float* cons
  * Allocation-free forward transform. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they transform, e.g.
  * code running inside a fixed memory budget, a host callback, or an arena that some
- * other component owns. It computes exactly what sl_forward computes, but calls no
- * cudaMalloc, cudaFree or other allocating routine: its scratch (the signal's
+ * other component owns. It computes the forward transform with sl_forward's FP32
+ * general-path kernels whatever the bank's path or precision mode (so it matches
+ * sl_forward within the parity tolerance, 1e-5 relative), but calls no cudaMalloc,
+ * cudaFree or other allocating routine: its scratch (the signal's
  * spectrum and the per-filter intermediate spectra) lives in one static device array
  * of SL_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library holds
  * until the process exits.

@@ -190,6 +190,11 @@ static double phi_resp(const FilterDesign* D, int J, int j, int d, int k, double
 std::vector<FilterDesc> enumerate_filters(const BankSpec& s) {
   std::vector<FilterDesc> out;
   out.push_back({-1, 0, 0, 0});
+  if (s.kind == kWavelets) {  // per scale, coarse to fine: g (x) h, h (x) g, g (x) g
+    for (int j = 0; j < s.J; ++j)
+      for (int o = 1; o <= 3; ++o) out.push_back({j, o, 0, 0});
+    return out;
+  }
   for (int j = 0; j < s.J; ++j) {
     const int e = 1 << s.d[j];
     if (s.ndim == 2) {
@@ -265,6 +270,22 @@ void BankEvaluator::eval_2d(const FilterDesc& f, double* out) const {
       const double a = resp_lowpass_j(D, s.J, 2.0 * kPi * i0 / n0);
       for (int64_t i1 = 0; i1 < nh; ++i1)
         out[i0 * nh + i1] = a * resp_lowpass_j(D, s.J, 2.0 * kPi * i1 / n1);
+    }
+    return;
+  }
+  if (s.kind == kWavelets) {
+    // the a trous stationary wavelet filters at level a = J - j (eq. lowhigh's h_a and
+    // g_a on each axis): cone 1 = g_a(xi_1) h_a(xi_2), 2 = h_a(xi_1) g_a(xi_2), 3 = g_a g_a
+    const int a = s.J - f.scale;
+    std::vector<double> r1(nh);
+    for (int64_t i1 = 0; i1 < nh; ++i1) {
+      const double x1 = 2.0 * kPi * i1 / n1;
+      r1[i1] = f.cone == 1 ? resp_lowpass_j(D, a, x1) : resp_highpass_j(D, a, x1);
+    }
+    for (int64_t i0 = 0; i0 < n0; ++i0) {
+      const double x0 = 2.0 * kPi * i0 / n0;
+      const double r0 = f.cone == 2 ? resp_lowpass_j(D, a, x0) : resp_highpass_j(D, a, x0);
+      for (int64_t i1 = 0; i1 < nh; ++i1) out[i0 * nh + i1] = r0 * r1[i1];
     }
     return;
   }

@@ -11,7 +11,8 @@ namespace sl {
 
 struct FilterDesc {
   int scale;  // 0..J-1, -1 for the lowpass
-  int cone;   // 2D: cone 1/2; 3D: pyramid 1..3; 0 for the lowpass
+  int cone;   // 2D: cone 1/2; 3D: pyramid 1..3; wavelets: 1 = g (x) h, 2 = h (x) g,
+              // 3 = g (x) g; 0 for the lowpass
   int k1;     // shear (2D) or first shear (3D)
   int k2;     // second shear (3D), 0 in 2D
 };
@@ -24,8 +25,15 @@ struct FilterDesign {
   int pr = 0, pc = 0;     // (axis 0 of P pairs with xi_1, axis 1 with xi_2)
 };
 
+// The filter systems a bank can hold.
+enum BankKind {
+  kShearlets = 0,  // the digital shearlet system (Defs. digitSH_alpha, 3DdigitSH_alpha)
+  kWavelets = 1    // the separable stationary wavelet system on the same QMF (2D only)
+};
+
 struct BankSpec {
   std::shared_ptr<const FilterDesign> design;  // null: built-in filters
+  int kind = kShearlets;
   int ndim = 2;
   int64_t dims[3] = {1, 1, 1};
   int J = 1;

@@ -875,5 +875,21 @@ __global__ void __launch_bounds__(256) k_inpaint_mix(const float* __restrict__ f
   }
 }
 
+// out = a - b over n elements (four per thread and step where aligned).
+__global__ void __launch_bounds__(256) k_sub(const float* __restrict__ a, const float* __restrict__ b,
+                                             float* __restrict__ out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * i < n; i += stride) {
+    const int64_t e = 4 * i;
+    if (e + 3 < n) {
+      const float4 u = reinterpret_cast<const float4*>(a)[i];
+      const float4 v = reinterpret_cast<const float4*>(b)[i];
+      reinterpret_cast<float4*>(out)[i] = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
+    } else {
+      for (int64_t k = e; k < n; ++k) out[k] = a[k] - b[k];
+    }
+  }
+}
+
 }  // namespace dev
 }  // namespace sl

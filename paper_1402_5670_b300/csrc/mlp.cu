@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -319,8 +320,14 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       smem_addr(bar)));
 }
 
-// Bounded wait for the mbarrier phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Default limit of a tensor-core wait: about two seconds of SM clock.
+constexpr long long kTcWaitCycles = 4000000000LL;
+
+// Bounded wait for the mbarrier phase with the given parity; false once `limit`
+// cycles have passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kTcWaitCycles) {
+  if (limit <= 0) return false;  // a zero budget gives up at once (test hook)
   uint32_t done = 0;
   const long long t0 = clock64();
   while (!done) {
@@ -329,7 +336,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(smem_addr(bar)), "r"(parity));
-    if (!done && clock64() - t0 > 4000000000LL) return false;  // about two seconds
+    if (!done && clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -481,7 +488,8 @@ __device__ __forceinline__ void gather_nb(const Geom& g, const float* __restrict
 
 template <int NDIM>
 __global__ void __launch_bounds__(TC_THREADS)
-    k_mlp_apply_tc(MlpArgs a, const TcWeights<NDIM>* __restrict__ wg, int* err) {
+    k_mlp_apply_tc(MlpArgs a, const TcWeights<NDIM>* __restrict__ wg, int* err,
+                   long long wait_limit) {
   using NN = Net<NDIM>;
   constexpr int F = NN::F, KP = NN::KP, NB = NN::NB;
   constexpr int CENTRE = NB / 2;  // offset (0, .., 0) in the row-major neighbourhood
@@ -578,7 +586,7 @@ __global__ void __launch_bounds__(TC_THREADS)
                   umma_desc(w1 + ks * 256, 128, (KP / 8) * 128), ks > 0);
       umma_commit(&S.bar);
     }
-    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0));
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0, wait_limit));
     tc_after_sync();
     if (!late) {
       // h1 = relu(z1) -> act, 32 columns at a time, then the bias ones
@@ -613,7 +621,7 @@ __global__ void __launch_bounds__(TC_THREADS)
                   umma_desc(w2 + ks * 256, 128, (K2 / 8) * 128), ks > 0);
       umma_commit(&S.bar);
     }
-    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1));
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
     tc_after_sync();
     if (!late) {
       float acc[4] = {S.w.b3[0], 0.f, 0.f, 0.f};  // four chains of 16
@@ -638,7 +646,9 @@ __global__ void __launch_bounds__(TC_THREADS)
   if (timed_out) {
     if (tid == 0) {
       atomicExch(err, 1);
-      mbar_wait(&S.bar, pending);  // let the MMAs in flight finish (bounded) before the free
+      // let the MMAs in flight finish (bounded by the default limit, whatever the
+      // per-tile limit was) before the tensor memory is freed
+      mbar_wait(&S.bar, pending);
     }
     __syncthreads();
   }
@@ -1249,6 +1259,11 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return mfail(SL_ECUDA, "cudaStreamIsCapturing");
   const bool repack = !M->tc_packed || M->pack_stream != st || cap != cudaStreamCaptureStatusNone;
   if (M->engine == SL_MLP_TCGEN05) {
+    // Per-tile wait limit in SM cycles: the default (about two seconds), or the value
+    // of SL_MLP_WAIT_CYCLES, a test hook that makes the waits run out on purpose so
+    // that the timeout path (flag, drain, free, sl_mlp_check) can be exercised.
+    long long limit = kTcWaitCycles;
+    if (const char* e = std::getenv("SL_MLP_WAIT_CYCLES")) limit = std::max(0LL, std::atoll(e));
     // the grid keeps every SM's CTAs within its 512 TMEM columns: no allocation waits
     if (M->ndim == 2) {
       const size_t sm = sizeof(TcApplySmem<2>);
@@ -1257,7 +1272,7 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
       auto* wt = reinterpret_cast<TcWeights<2>*>(M->tc_pack);
       if (repack)
         k_mlp_pack_tc<2><<<(tc_pack_elems<2>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
-      k_mlp_apply_tc<2><<<apply_tc_grid<2>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
+      k_mlp_apply_tc<2><<<apply_tc_grid<2>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err, limit);
     } else {
       const size_t sm = sizeof(TcApplySmem<3>);
       cudaFuncSetAttribute(k_mlp_apply_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1265,7 +1280,7 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
       auto* wt = reinterpret_cast<TcWeights<3>*>(M->tc_pack);
       if (repack)
         k_mlp_pack_tc<3><<<(tc_pack_elems<3>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
-      k_mlp_apply_tc<3><<<apply_tc_grid<3>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err);
+      k_mlp_apply_tc<3><<<apply_tc_grid<3>(), TC_THREADS, sm, st>>>(a, wt, M->tc_err, limit);
     }
   } else {
     const int grid = 4 * sm_count();

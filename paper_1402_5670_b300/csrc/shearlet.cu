@@ -658,9 +658,33 @@ sl_status sl_build_filters_ex(int ndim, const int64_t* dims, int nScales, const 
                                out);
 }
 
+static sl_status build_filters_impl(int kind, int ndim, const int64_t* dims, int nScales,
+                                    const int* shearLevels, int fullSystem, int device,
+                                    const sl_options* opt, const sl_filters* filters,
+                                    sl_bank** out);
+
 sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales, const int* shearLevels,
                                 int fullSystem, int device, const sl_options* opt,
                                 const sl_filters* filters, sl_bank** out) {
+  return build_filters_impl(sl::kShearlets, ndim, dims, nScales, shearLevels, fullSystem, device,
+                            opt, filters, out);
+}
+
+sl_status sl_build_wavelets(int ndim, const int64_t* dims, int nScales, int device,
+                            const sl_filters* filters, sl_bank** out) {
+  if (ndim != 2) return fail(ndim == 3 ? SL_ENOTSUP : SL_EINVAL, "wavelet banks are 2D");
+  if (filters && filters->fan) return fail(SL_EINVAL, "a wavelet bank takes no fan filter");
+  const int zeros[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  return build_filters_impl(sl::kWavelets, ndim, dims, nScales, zeros, 0, device, nullptr,
+                            filters, out);
+}
+
+}  // extern "C"
+
+static sl_status build_filters_impl(int kind, int ndim, const int64_t* dims, int nScales,
+                                    const int* shearLevels, int fullSystem, int device,
+                                    const sl_options* opt, const sl_filters* filters,
+                                    sl_bank** out) {
   if (!out) return fail(SL_EINVAL, "out is NULL");
   *out = nullptr;
   std::shared_ptr<sl::FilterDesign> design;
@@ -690,6 +714,7 @@ sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales, cons
   if (nScales < 1 || nScales > 8) return fail(SL_EINVAL, "nScales must be in [1, 8]");
   sl::BankSpec spec;
   spec.design = design;
+  spec.kind = kind;
   spec.ndim = ndim;
   spec.J = nScales;
   spec.full = fullSystem != 0;
@@ -833,6 +858,8 @@ sl_status sl_build_filters_user(int ndim, const int64_t* dims, int nScales, cons
   *out = b.release();
   return SL_OK;
 }
+
+extern "C" {
 
 void sl_free_filters(sl_bank* bank) {
   if (!bank) return;
@@ -1045,10 +1072,11 @@ static sl_status spectrum_of(const Plan& P, const float* x, cudaStream_t st) {
 }
 
 // Per-filter last-axes pass of one group: ROW_C2R (coefficients out), ROW_R2C
-// (coefficients in) or ROW_RT (scratch in place, thresholded).
+// (coefficients in) or ROW_RT (scratch in place, thresholded). creal_in / creal_out
+// address the plane of the group's first filter.
 template <int MODE>
-static sl_status slab_pass(const Plan& P, int j0, int nf, const float* creal_in,
-                           float* creal_out, const Thresholds* thr, cudaStream_t st) {
+static sl_status slab_pass(const Plan& P, int nf, const float* creal_in, float* creal_out,
+                           const Thresholds* thr, cudaStream_t st) {
   RowArgs ra{};
   ra.scale = (float)(1.0 / (double)P.N);
   if (thr) {
@@ -1058,10 +1086,10 @@ static sl_status slab_pass(const Plan& P, int j0, int nf, const float* creal_in,
   if (MODE == sl::dev::ROW_C2R) {
     ra.in_half = P.scratch;
     ra.in_stride = P.Nhp;
-    ra.out_real = creal_out + (int64_t)j0 * P.N;
+    ra.out_real = creal_out;
     ra.out_stride = P.N;
   } else if (MODE == sl::dev::ROW_R2C) {
-    ra.in_real = creal_in + (int64_t)j0 * P.N;
+    ra.in_real = creal_in;
     ra.in_stride = P.N;
     ra.out_half = P.scratch;
     ra.out_stride = P.Nhp;
@@ -1119,20 +1147,22 @@ static sl_status inv_acc_pass(const Plan& P, int g_idx, int j0, int nf, cudaStre
                   "col_inv_accumulate");
 }
 
-// Partials [0, nparts) -> (sum, times 1/Psi in FP64 for the inverse) -> inverse FFT
-// along the pencils -> last axes -> real x.
-static sl_status inv_final(const Plan& P, int nparts, bool use_invpsi, float* x,
-                           cudaStream_t st) {
+// out = (sum of the spectra parts[0, nparts), `stride` elements apart) times 1/Psi in
+// FP64 when use_invpsi: one tile-major spectrum.
+static sl_status reduce_spectra(const Plan& P, const float2* parts, int nparts, int64_t stride,
+                                bool use_invpsi, float2* out, cudaStream_t st) {
   const int64_t n = P.Nhp;
   const int grid = (int)std::min<int64_t>((n / 2 + 255) / 256, 4 * 148);
-  const float2* parts = P.partial;
   const double* w = use_invpsi ? P.invPsi : nullptr;
-  float2* out = P.xhat;
   g_next_bytes = use_invpsi ? 8.0 * (double)P.Nh : 0.0;  // 1/Psi read
-  SL_TRY(launched(timed_launch("reduce_partials", st, [&]() {
-                    sl::dev::k_reduce_parts<<<grid, 256, 0, st>>>(parts, nparts, n, w, out, n);
+  return launched(timed_launch("reduce_partials", st, [&]() {
+                    sl::dev::k_reduce_parts<<<grid, 256, 0, st>>>(parts, nparts, stride, w, out, n);
                   }),
-                  "reduce_partials"));
+                  "reduce_partials");
+}
+
+// Spectrum P.xhat -> inverse FFT along the pencils -> last axes -> real x.
+static sl_status spectrum_to_signal(const Plan& P, float* x, cudaStream_t st) {
   ColArgs ca{};
   ca.in = P.xhat;
   ca.out = P.xhat;
@@ -1148,13 +1178,29 @@ static sl_status inv_final(const Plan& P, int nparts, bool use_invpsi, float* x,
   return last_axes<sl::dev::ROW_C2R>(P, ra, 1, st);
 }
 
+// Spectra parts[0, nparts) -> (sum, times 1/Psi in FP64 for the inverse) -> inverse
+// FFT along the pencils -> last axes -> real x.
+static sl_status parts_to_signal(const Plan& P, const float2* parts, int nparts,
+                                 bool use_invpsi, float* x, cudaStream_t st) {
+  SL_TRY(reduce_spectra(P, parts, nparts, P.Nhp, use_invpsi, P.xhat, st));
+  return spectrum_to_signal(P, x, st);
+}
+
+static sl_status inv_final(const Plan& P, int nparts, bool use_invpsi, float* x,
+                           cudaStream_t st) {
+  return parts_to_signal(P, P.partial, nparts, use_invpsi, x, st);
+}
+
 // Partials are written compactly: group g uses parts [g*S, g*S + splits_g). Every
 // group but the last holds G filters and so uses all S of its parts; the used parts
 // are therefore the contiguous range [0, parts_used).
-static int parts_used(const Plan& P) {
-  const int last = P.R - (P.ngroups - 1) * P.G;
-  return (P.ngroups - 1) * P.S + (last + P.fps - 1) / P.fps;
+static int parts_used(const Plan& P, int nfilters) {
+  if (nfilters <= 0) return 0;
+  const int ng = (nfilters + P.G - 1) / P.G;
+  const int last = nfilters - (ng - 1) * P.G;
+  return (ng - 1) * P.S + (last + P.fps - 1) / P.fps;
 }
+static int parts_used(const Plan& P) { return parts_used(P, P.R); }
 
 static void fill_thresholds(const sl_bank* b, int j0, int nf, float sigma, const float* K,
                             Thresholds* t) {
@@ -1164,39 +1210,54 @@ static void fill_thresholds(const sl_bank* b, int j0, int nf, float sigma, const
   }
 }
 
+// Filters [j0, j1) from the spectrum P.xhat: coeffs holds their planes [j1 - j0][dims].
+static sl_status forward_filters(const Plan& P, int j0, int j1, float* coeffs, cudaStream_t st) {
+  for (int j = j0; j < j1; j += P.G) {
+    const int nf = std::min(P.G, j1 - j);
+    SL_TRY(fwd_filter_pass(P, j, nf, st));
+    SL_TRY(slab_pass<sl::dev::ROW_C2R>(P, nf, nullptr, coeffs + (int64_t)(j - j0) * P.N, nullptr, st));
+  }
+  return SL_OK;
+}
+
 static sl_status forward_plan(const Plan& P, const float* x, float* coeffs, cudaStream_t st) {
   SL_TRY(spectrum_of(P, x, st));
-  for (int g = 0; g < P.ngroups; ++g) {
-    const int j0 = g * P.G;
-    const int nf = std::min(P.G, P.R - j0);
-    SL_TRY(fwd_filter_pass(P, j0, nf, st));
-    SL_TRY(slab_pass<sl::dev::ROW_C2R>(P, j0, nf, nullptr, coeffs, nullptr, st));
+  return forward_filters(P, 0, P.R, coeffs, st);
+}
+
+// sum_{j in [j0, j1)} psi_hat_j FFT(C_j) as partial spectra [0, parts_used(P, j1 - j0))
+// in P.partial; coeffs holds the planes [j1 - j0][dims].
+static sl_status backward_filters(const Plan& P, const float* coeffs, int j0, int j1,
+                                  cudaStream_t st) {
+  for (int j = j0, g = 0; j < j1; j += P.G, ++g) {
+    const int nf = std::min(P.G, j1 - j);
+    SL_TRY(slab_pass<sl::dev::ROW_R2C>(P, nf, coeffs + (int64_t)(j - j0) * P.N, nullptr, nullptr, st));
+    SL_TRY(inv_acc_pass(P, g, j, nf, st));
   }
   return SL_OK;
 }
 
 static sl_status backward(const Plan& P, const float* coeffs, float* x, bool use_invpsi,
                           cudaStream_t st) {
-  for (int g = 0; g < P.ngroups; ++g) {
-    const int j0 = g * P.G;
-    const int nf = std::min(P.G, P.R - j0);
-    SL_TRY(slab_pass<sl::dev::ROW_R2C>(P, j0, nf, coeffs, nullptr, nullptr, st));
-    SL_TRY(inv_acc_pass(P, g, j0, nf, st));
-  }
+  SL_TRY(backward_filters(P, coeffs, 0, P.R, st));
   return inv_final(P, parts_used(P), use_invpsi, x, st);
 }
 
 // Fused denoise: per group, filter, C2R + threshold + R2C in shared memory, accumulate.
+// lowpass_thr: threshold of the lowpass subband (0 keeps it whole, as the denoising rule
+// does; +infinity drops it).
 static sl_status denoise_plan(const Plan& P, const float* noisy, float* out, float sigma,
-                              const float* K, cudaStream_t st) {
+                              const float* K, cudaStream_t st, float lowpass_thr = 0.f) {
   SL_TRY(spectrum_of(P, noisy, st));
   for (int g = 0; g < P.ngroups; ++g) {
     const int j0 = g * P.G;
     const int nf = std::min(P.G, P.R - j0);
     Thresholds t;
     fill_thresholds(P.bank, j0, nf, sigma, K, &t);
+    for (int i = 0; i < nf; ++i)
+      if (P.bank->filt[j0 + i].scale < 0) t.v[i] = lowpass_thr;
     SL_TRY(fwd_filter_pass(P, j0, nf, st));
-    SL_TRY(slab_pass<sl::dev::ROW_RT>(P, j0, nf, nullptr, nullptr, &t, st));
+    SL_TRY(slab_pass<sl::dev::ROW_RT>(P, nf, nullptr, nullptr, &t, st));
     SL_TRY(inv_acc_pass(P, g, j0, nf, st));
   }
   return inv_final(P, parts_used(P), true, out, st);
@@ -1278,6 +1339,70 @@ sl_status sl_inverse(const sl_bank* b, const float* coeffs, float* x, void* stre
   return backward(plan_of(b), coeffs, x, true, (cudaStream_t)stream);
 }
 
+// ------------------------------------------------ filter-sharded transform ---
+// The inverse is a sum over filters (eq. reconstruction, Algorithm 2), so one large
+// transform splits over ranks by filter ranges: every rank turns its coefficients
+// into a partial spectrum, the partials are summed (one reduction of a spectrum),
+// and one rank divides by Psi and transforms back. The forward needs the signal's
+// spectrum on every rank (one broadcast) and then produces each range independently.
+
+static sl_status check_range(const sl_bank* b, int j0, int j1) {
+  if (j0 < 0 || j1 < j0 || j1 > b->R)
+    return fail(SL_EINVAL, "filter range must satisfy 0 <= j0 <= j1 <= R");
+  return SL_OK;
+}
+
+sl_status sl_spectrum_points(const sl_bank* b, int64_t* n_points) {
+  if (!b || !n_points) return fail(SL_EINVAL, "bank or n_points is NULL");
+  *n_points = b->Nhp;
+  return SL_OK;
+}
+
+sl_status sl_spectrum(const sl_bank* b, const float* x, float* xhat, void* stream) {
+  SL_TRY(check_call(b));
+  if (!x || !xhat) return fail(SL_EINVAL, "x or xhat is NULL");
+  SL_TRY(check_aligned(x, xhat));
+  Plan P = plan_of(b);
+  P.xhat = reinterpret_cast<float2*>(xhat);
+  return spectrum_of(P, x, (cudaStream_t)stream);
+}
+
+sl_status sl_forward_range(const sl_bank* b, const float* xhat, int j0, int j1, float* coeffs,
+                           void* stream) {
+  SL_TRY(check_call(b));
+  SL_TRY(check_range(b, j0, j1));
+  if (!xhat || (!coeffs && j1 > j0)) return fail(SL_EINVAL, "xhat or coeffs is NULL");
+  SL_TRY(check_aligned(xhat, coeffs));
+  Plan P = plan_of(b);
+  P.xhat = reinterpret_cast<float2*>(const_cast<float*>(xhat));  // read only
+  return forward_filters(P, j0, j1, coeffs, (cudaStream_t)stream);
+}
+
+sl_status sl_inverse_partial(const sl_bank* b, const float* coeffs, int j0, int j1,
+                             float* partial, void* stream) {
+  SL_TRY(check_call(b));
+  SL_TRY(check_range(b, j0, j1));
+  if (!partial || (!coeffs && j1 > j0)) return fail(SL_EINVAL, "coeffs or partial is NULL");
+  SL_TRY(check_aligned(coeffs, partial));
+  Plan P = plan_of(b);
+  cudaStream_t st = (cudaStream_t)stream;
+  float2* out = reinterpret_cast<float2*>(partial);
+  if (j1 == j0)
+    return launched(cudaMemsetAsync(out, 0, (size_t)P.Nhp * sizeof(float2), st), "zero partial");
+  SL_TRY(backward_filters(P, coeffs, j0, j1, st));
+  return reduce_spectra(P, P.partial, parts_used(P, j1 - j0), P.Nhp, false, out, st);
+}
+
+sl_status sl_inverse_finish(const sl_bank* b, const float* summed, int dual, float* x,
+                            void* stream) {
+  SL_TRY(check_call(b));
+  if (!summed || !x) return fail(SL_EINVAL, "summed or x is NULL");
+  SL_TRY(check_aligned(summed, x));
+  Plan P = plan_of(b);
+  return parts_to_signal(P, reinterpret_cast<const float2*>(summed), 1, dual != 0, x,
+                         (cudaStream_t)stream);
+}
+
 sl_status sl_threshold(const sl_bank* b, float* coeffs, float sigma, const float* K,
                        void* stream) {
   SL_TRY(check_call(b));
@@ -1349,6 +1474,59 @@ sl_status sl_inpaint(const sl_bank* cb, const float* f_masked, const uint8_t* ma
                     }),
                     "inpaint_mix"));
     SL_TRY(denoise_plan(P, u, out, (float)delta, ones.data(), st));
+    delta *= lam;
+  }
+  return SL_OK;
+}
+
+sl_status sl_decompose(const sl_bank* ccurv, const sl_bank* iso, const float* f, float* f0,
+                       float* f1, float delta_init, float delta_min, int iterations,
+                       void* stream) {
+  SL_TRY(check_call(ccurv));
+  SL_TRY(check_call(iso));
+  if (!f || !f0 || !f1) return fail(SL_EINVAL, "f, f0 or f1 is NULL");
+  if (ccurv->spec.ndim != iso->spec.ndim || ccurv->N != iso->N ||
+      ccurv->spec.dims[0] != iso->spec.dims[0] || ccurv->spec.dims[1] != iso->spec.dims[1] ||
+      ccurv->spec.dims[2] != iso->spec.dims[2] || ccurv->device != iso->device)
+    return fail(SL_EINVAL, "the two banks must share grid and device");
+  if (f0 == f1 || (const float*)f0 == f || (const float*)f1 == f)
+    return fail(SL_EINVAL, "f, f0 and f1 must be distinct arrays");
+  SL_TRY(check_aligned(f, f0));
+  SL_TRY(check_aligned(f1, f1));
+  if (iterations < 1) return fail(SL_EINVAL, "iterations must be >= 1");
+  if (!(delta_init > 0.f) || !(delta_min > 0.f) || !std::isfinite(delta_init) ||
+      !std::isfinite(delta_min))
+    return fail(SL_EINVAL, "delta_init and delta_min must be finite and > 0");
+  sl_bank* b = const_cast<sl_bank*>(ccurv);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!b->inp_u && cudaMalloc((void**)&b->inp_u, (size_t)b->N * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    b->inp_u = nullptr;
+    return fail(SL_ENOMEM, "allocating the decomposition buffer");
+  }
+  const double lam = iterations > 1 ? std::pow((double)delta_min / (double)delta_init,
+                                               1.0 / (double)(iterations - 1))
+                                    : 1.0;
+  std::vector<float> ones0((size_t)b->spec.J, 1.0f), ones1((size_t)iso->spec.J, 1.0f);
+  const Plan P0 = plan_of(b), P1 = plan_of(iso);
+  const int64_t n = b->N;
+  const int grid = (int)std::min<int64_t>((n / 4 + 255) / 256, 4 * 148);
+  float* u = b->inp_u;
+  SL_CUDA(cudaMemsetAsync(f1, 0, (size_t)n * sizeof(float), st));
+  double delta = delta_init;
+  for (int it = 0; it < iterations; ++it) {
+    const float* other[2] = {f1, f0};
+    for (int part = 0; part < 2; ++part) {
+      const float* g = other[part];
+      SL_TRY(launched(timed_launch("decompose_residual", st, [&]() {
+                        sl::dev::k_sub<<<grid, 256, 0, st>>>(f, g, u, n);
+                      }),
+                      "decompose_residual"));
+      if (part == 0)
+        SL_TRY(denoise_plan(P0, u, f0, (float)delta, ones0.data(), st, INFINITY));
+      else
+        SL_TRY(denoise_plan(P1, u, f1, (float)delta, ones1.data(), st));
+    }
     delta *= lam;
   }
   return SL_OK;

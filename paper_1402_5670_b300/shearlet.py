@@ -39,6 +39,10 @@ SIGNATURES = {
     "sl_build_filters_ex": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, _c_int_p,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.POINTER(_vp)]),
+    "sl_build_wavelets": (ctypes.c_int, [ctypes.c_int, _c_int64_p, ctypes.c_int, ctypes.c_int, _vp,
+                                         ctypes.POINTER(_vp)]),
+    "sl_decompose": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_int, _vp]),
     "sl_free_filters": (None, [_vp]),
     "sl_bank_info": (ctypes.c_int, [_vp, _c_int_p, _c_int64_p, _c_int_p, _c_int_p]),
     "sl_bank_filter_meta": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
@@ -55,6 +59,11 @@ SIGNATURES = {
     "sl_denoise": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, _c_float_p, _vp]),
     "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sl_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sl_spectrum_points": (ctypes.c_int, [_vp, _c_int64_p]),
+    "sl_spectrum": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_forward_range": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "sl_inverse_partial": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "sl_inverse_finish": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
     "sl_inpaint": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_int,
                                   _vp]),
     "sl_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
@@ -201,6 +210,22 @@ def sl_build_filters_ex(dims: Sequence[int], n_scales: int, shear_levels: Sequen
     return out.value
 
 
+def sl_build_wavelets(dims: Sequence[int], n_scales: int, device: int = 0, qmf=None) -> int:
+    """The separable stationary wavelet bank (sl_build_wavelets), optionally on a user QMF."""
+    nd = len(dims)
+    d = (ctypes.c_int64 * nd)(*[int(v) for v in dims])
+    out = _vp()
+    f = None
+    if qmf is not None:
+        h = np.ascontiguousarray(qmf, dtype=np.float64).ravel()
+        f = sl_filters()
+        f.qmf, f.qmf_len = h.ctypes.data_as(_c_double_p), h.size
+    _check(lib().sl_build_wavelets(nd, d, int(n_scales), int(device),
+                                   ctypes.byref(f) if f is not None else None, ctypes.byref(out)),
+           "sl_build_wavelets")
+    return out.value
+
+
 def sl_free_filters(bank: int) -> None:
     lib().sl_free_filters(bank)
 
@@ -235,6 +260,29 @@ def sl_forward_noalloc(bank: int, psi, x, coeffs, stream=None) -> None:
     """Forward transform that allocates nothing (static device scratch); psi, x and
     coeffs are device pointers owned by the caller."""
     _check(lib().sl_forward_noalloc(bank, psi, x, coeffs, stream), "sl_forward_noalloc")
+
+
+def sl_spectrum_points(bank: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().sl_spectrum_points(bank, ctypes.byref(n)), "sl_spectrum_points")
+    return n.value
+
+
+def sl_spectrum(bank: int, x, xhat, stream=None) -> None:
+    _check(lib().sl_spectrum(bank, x, xhat, stream), "sl_spectrum")
+
+
+def sl_forward_range(bank: int, xhat, j0: int, j1: int, coeffs, stream=None) -> None:
+    _check(lib().sl_forward_range(bank, xhat, int(j0), int(j1), coeffs, stream), "sl_forward_range")
+
+
+def sl_inverse_partial(bank: int, coeffs, j0: int, j1: int, partial, stream=None) -> None:
+    _check(lib().sl_inverse_partial(bank, coeffs, int(j0), int(j1), partial, stream),
+           "sl_inverse_partial")
+
+
+def sl_inverse_finish(bank: int, summed, dual: bool, x, stream=None) -> None:
+    _check(lib().sl_inverse_finish(bank, summed, int(bool(dual)), x, stream), "sl_inverse_finish")
 
 
 def sl_error_stats(y, ref, stream=None) -> dict:
@@ -292,6 +340,22 @@ class Bank:
         self.path = path
         self.handle = sl_build_filters_ex(dims, n_scales, shear_levels, full_system, device, path,
                                           precision, qmf, fan)
+        self._describe(device)
+
+    @classmethod
+    def wavelets(cls, dims: Sequence[int], n_scales: int, device: int = 0, qmf=None) -> "Bank":
+        """The separable stationary wavelet bank on the same grid (sl_build_wavelets):
+        lowpass, then per scale coarse to fine g(x)h, h(x)g, g(x)g; R = 1 + 3 n_scales."""
+        if device >= 0:
+            import torch
+            torch.cuda.set_device(device)
+        b = cls.__new__(cls)
+        b.path = "auto"
+        b.handle = sl_build_wavelets(dims, n_scales, device, qmf)
+        b._describe(device)
+        return b
+
+    def _describe(self, device: int) -> None:
         L = lib()
         nd, R, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         dd = (ctypes.c_int64 * 3)()
@@ -364,6 +428,43 @@ class Bank:
                    _dev_ptr(out, "x", self.N), _stream_ptr(stream))
         return out
 
+    # -------- filter ranges (one transform sharded over ranks) --------
+
+    @property
+    def spectrum_points(self) -> int:
+        """Complex points of one spectrum buffer (library layout)."""
+        return sl_spectrum_points(self.handle)
+
+    def spectrum(self, x, out=None, stream=None):
+        """X_hat = FFT(x) as a float32 tensor of 2 * spectrum_points (sl_spectrum)."""
+        n = 2 * self.spectrum_points
+        out = self._empty((n,)) if out is None else out
+        sl_spectrum(self.handle, _dev_ptr(x, "x", self.N), _dev_ptr(out, "xhat", n),
+                    _stream_ptr(stream))
+        return out
+
+    def forward_range(self, xhat, j0: int, j1: int, out=None, stream=None):
+        """Coefficients of filters [j0, j1) from a spectrum (sl_forward_range)."""
+        out = self._empty((j1 - j0,) + self.dims) if out is None else out
+        sl_forward_range(self.handle, _dev_ptr(xhat, "xhat", 2 * self.spectrum_points), j0, j1,
+                         _dev_ptr(out, "coeffs", (j1 - j0) * self.N), _stream_ptr(stream))
+        return out
+
+    def inverse_partial(self, coeffs, j0: int, j1: int, out=None, stream=None):
+        """sum_{j in [j0, j1)} FFT(C_j) psi_hat_j as a spectrum (sl_inverse_partial)."""
+        n = 2 * self.spectrum_points
+        out = self._empty((n,)) if out is None else out
+        sl_inverse_partial(self.handle, _dev_ptr(coeffs, "coeffs", (j1 - j0) * self.N), j0, j1,
+                           _dev_ptr(out, "partial", n), _stream_ptr(stream))
+        return out
+
+    def inverse_finish(self, summed, dual: bool = True, out=None, stream=None):
+        """x from the sum of all partials: / Psi (dual) or not (adjoint) (sl_inverse_finish)."""
+        out = self._empty(self.dims) if out is None else out
+        sl_inverse_finish(self.handle, _dev_ptr(summed, "summed", 2 * self.spectrum_points), dual,
+                          _dev_ptr(out, "x", self.N), _stream_ptr(stream))
+        return out
+
     def threshold_(self, coeffs, sigma: float, K: Sequence[float], stream=None):
         self._check_K(K)
         sl_threshold(self.handle, _dev_ptr(coeffs, "coeffs", self.R * self.N), sigma, K,
@@ -389,6 +490,18 @@ class Bank:
                                 _dev_ptr(out, "out", self.N), float(delta_init), float(delta_min),
                                 int(iterations), _stream_ptr(stream)), "sl_inpaint")
         return out
+
+    def decompose(self, iso: "Bank", f, delta_init: float, delta_min: float, iterations: int,
+                  out0=None, out1=None, stream=None):
+        """Image decomposition (sl_decompose) of f into the curvilinear part (this
+        shearlet bank) and the isotropic part (iso, a wavelet bank): returns (f0, f1)."""
+        out0 = self._empty(self.dims) if out0 is None else out0
+        out1 = self._empty(self.dims) if out1 is None else out1
+        _check(lib().sl_decompose(self.handle, iso.handle, _dev_ptr(f, "f", self.N),
+                                  _dev_ptr(out0, "f0", self.N), _dev_ptr(out1, "f1", self.N),
+                                  float(delta_init), float(delta_min), int(iterations),
+                                  _stream_ptr(stream)), "sl_decompose")
+        return out0, out1
 
     def fwdinv_host(self, x_host, y_host, stream=None):
         """Round trip from host memory (x_host, y_host: pinned CPU float32 tensors)."""

@@ -88,6 +88,36 @@ def moving_ellipses_volume(shape: Sequence[int], seed: int) -> np.ndarray:
     return vol
 
 
+def points_and_curves(shape: Sequence[int], seed: int, n_curves: int = 4, n_points: int = 40,
+                      peak: float = 255.0) -> Tuple[np.ndarray, np.ndarray]:
+    """The two binary parts of a decomposition test image (Sec. 5.5 separates an image
+    of curves and points): (curves, points), float32 with values 0 and ``peak``.
+    curves: ``n_curves`` sine-shaped curves y = a sin(w x + phi) + b about 1.5 pixels
+    thick, half of them drawn along the other axis; points: ``n_points`` disks of
+    radius U[1.5, 3]. The image to decompose is their sum."""
+    n0, n1 = int(shape[0]), int(shape[1])
+    r = _rng(seed)
+    y, x = np.meshgrid(np.arange(n0, dtype=np.float64), np.arange(n1, dtype=np.float64),
+                       indexing="ij")
+    curves = np.zeros((n0, n1), dtype=bool)
+    for i in range(int(n_curves)):
+        u, v, nu, nv = (y, x, n0, n1) if i % 2 == 0 else (x, y, n1, n0)
+        a = r.uniform(0.05, 0.2) * nu
+        w = r.uniform(0.5, 2.0) * 2 * np.pi / nv
+        phi = r.uniform(0, 2 * np.pi)
+        b = r.uniform(0.2, 0.8) * nu
+        # distance to the curve along u, scaled by the local slope
+        slope = a * w * np.cos(w * v + phi)
+        dist = np.abs(u - (a * np.sin(w * v + phi) + b)) / np.sqrt(1.0 + slope * slope)
+        curves |= dist <= 0.75
+    points = np.zeros((n0, n1), dtype=bool)
+    for _ in range(int(n_points)):
+        cy, cx = r.uniform(0, n0), r.uniform(0, n1)
+        rad = r.uniform(1.5, 3.0)
+        points |= (y - cy) ** 2 + (x - cx) ** 2 <= rad * rad
+    return (peak * curves).astype(np.float32), (peak * points).astype(np.float32)
+
+
 def add_noise(x: np.ndarray, sigma: float, seed: int) -> np.ndarray:
     """x + e with e ~ N(0, sigma^2) i.i.d. (Sec. 5.3); not clipped (float32)."""
     r = _rng(seed)

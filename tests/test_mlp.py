@@ -241,6 +241,32 @@ def test_apply_in_a_graph_follows_parameter_updates():
 
 
 @pytest.mark.gpu
+def test_tensor_core_wait_timeout_is_reported_and_recovers(monkeypatch):
+    """The bounded tensor-core waits of the tcgen05 engine, made to run out at once
+    (SL_MLP_WAIT_CYCLES=0, a test hook): the call returns, sl_mlp_check reports the
+    flag (and clears it), and the next call with the normal limit matches the
+    result from before bit for bit. Nothing here faults or hangs: the kernel drains
+    the MMAs it issued, with the normal limit, before it frees tensor memory."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5670_b300.shearlet import ShearletError
+    dims, J, sl = (64, 64), 2, (1, 1)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 7)
+    mlp.set_engine("tcgen05")
+    ref = mlp.apply(Cn, 20.0).clone()
+    mlp.check()
+    monkeypatch.setenv("SL_MLP_WAIT_CYCLES", "0")
+    mlp.apply(Cn, 20.0)
+    with pytest.raises(ShearletError):
+        mlp.check()
+    monkeypatch.delenv("SL_MLP_WAIT_CYCLES")
+    mlp.check()  # the flag was cleared
+    again = mlp.apply(Cn, 20.0)
+    mlp.check()
+    assert torch.equal(again, ref)
+
+
+@pytest.mark.gpu
 def test_learned_shrinkage_beats_hard_thresholding():
     """Trained on the GPU from transform-generated pairs, the learned gain must denoise
     held-out synthetic images better (PSNR) than the paper's hard threshold at every

@@ -46,6 +46,26 @@ def test_noalloc_forward_matches_forward_twice(case):
             assert rel(out, ref) < TOL
 
 
+def test_noalloc_on_tensor_core_bank_matches_fp32_forward():
+    """On a bank built in the BF16 tensor-core mode the allocation-free call still runs
+    the FP32 kernels: its result matches the FP32 bank's sl_forward to 1e-5, twice."""
+    from paper_1402_5670_b300 import shearlet as S
+    from paper_1402_5670_b300 import synth
+    dims, J, sl = (256, 256), 3, (1, 1, 2)
+    x = torch.from_numpy(synth.add_noise(synth.piecewise_smooth_image(dims, 6), 20.0, 7)).cuda()
+    with S.Bank(dims, J, sl, device=0) as bf:
+        ref = bf.forward(x)
+    with S.Bank(dims, J, sl, device=0, precision="tc_bf16") as bt:
+        assert bt.precision == "tc_bf16"
+        psi = torch.from_numpy(bt.filters_f32()).cuda().contiguous()
+        for _ in range(2):
+            out = torch.full((bt.R,) + dims, float("nan"), device="cuda")
+            S.sl_forward_noalloc(bt.handle, psi.data_ptr(), x.data_ptr(), out.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            assert rel(out, ref) < TOL
+
+
 def test_noalloc_with_host_only_bank():
     """A host-only bank allocates no device memory; the caller supplies the filters
     (here evaluated in FP64 on the host and rounded to FP32)."""
