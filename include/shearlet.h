@@ -258,6 +258,47 @@ sl_status sl_inverse_partial(const sl_bank* bank, const float* coeffs, int j0, i
 sl_status sl_inverse_finish(const sl_bank* bank, const float* summed, int dual, float* x,
                             void* stream);
 
+/* -------------------------------------------------- subsampled transform ---
+ * The digital shearlet transform with sampling (Defs. digitSH, digitSH_alpha: the
+ * coefficients of scale j are taken on a lattice given by the sampling matrix
+ * M_{c_j}), 2D banks only. Reading of the sampling: subband j of scale s(j) keeps
+ * the points of (step_j Z)^2 with step_j = 2^(J-1-s(j)) (the finest scale keeps every
+ * point), and the lowpass those of (2^(J-1) Z)^2. Grid sides must be multiples of
+ * 2^(J-1) (SL_ENOTSUP otherwise). Coefficients are stored compactly: subband j as a
+ * row-major [n0 / step_j][n1 / step_j] block at offset_j of one float array of
+ * offset_R floats (sl_sub_layout). With sampling there is no direct inverse
+ * (Sec. 3.4): sl_inverse_sub solves the frame equation by conjugate gradients.
+ * The first call of sl_forward_sub, sl_adjoint_sub or sl_inverse_sub on a bank
+ * allocates its working memory there: a full coefficient stack (R N floats), five
+ * [dims] vectors and the FP64 preconditioner table.
+ */
+
+/* step[R] (lattice step of each subband) and offset[R + 1] (compact offsets; offset[R]
+ * is the total count); host arrays, either may be NULL. Host-only banks work too. */
+sl_status sl_sub_layout(const sl_bank* bank, int* step, int64_t* offset);
+
+/* Subsampled forward transform: x DEVICE [dims] -> coeffs_sub DEVICE [offset_R]. */
+sl_status sl_forward_sub(const sl_bank* bank, const float* x, float* coeffs_sub, void* stream);
+
+/* Its adjoint: coeffs_sub -> x = sum_j psi_j * (coefficients of subband j on its
+ * lattice, zero elsewhere) (DEVICE arrays). */
+sl_status sl_adjoint_sub(const sl_bank* bank, const float* coeffs_sub, float* x, void* stream);
+
+/* Inverse of the subsampled transform by conjugate gradients (the frame algorithms of
+ * Sec. 2.1 and the CG inversion of Sec. 3.4): solves S x = T_sub* c with
+ * S = T_sub* T_sub, starting from x = 0, for exactly `iterations` steps. Each step is
+ * one fused pass for S p (forward, lattice mask and adjoint with the coefficients kept
+ * on chip), FP64 inner products and, if `precondition` is nonzero, the preconditioner
+ * z = IFFT(FFT(r) / Psi_sub), Psi_sub = sum_j |psi_hat_j|^2 / step_j^2 (FP64): the
+ * frame weight of eq. frame_filter with each subband's sampling density, which equals
+ * S when nothing is subsampled. Measured on a 256^2 four-scale bank: preconditioned,
+ * about ten steps reach the FP32 limit; plain CG needs several times more.
+ * rel_residual (host, may be NULL) receives ||T_sub* c - S x|| / ||T_sub* c|| after the
+ * last step; passing it synchronises the stream. Step sizes stay on the device (no
+ * host round trip per step). */
+sl_status sl_inverse_sub(const sl_bank* bank, const float* coeffs_sub, float* x, int iterations,
+                         int precondition, double* rel_residual, void* stream);
+
 /*
  * Hard thresholding in place (eq. hard_tresholding, Sec. 5.3): for every filter
  * j >= 1, C_j(m) = 0 unless |C_j(m)| >= K[scale(j)] * sigma * ||psi_j||_2. The lowpass

@@ -723,6 +723,82 @@ def inverse_finish(acc: np.ndarray, sysm: ShearletSystem, dual: bool = True) -> 
     return np.real(_dft.ifftn(acc / sysm.Psi if dual else acc))
 
 
+# --------------------------------------------------------------------------------
+# Subsampled transform and its inversion by conjugate gradients (Defs. digitSH,
+# digitSH_alpha with sampling; Sec. 3.4; the frame algorithms of Sec. 2.1)
+# --------------------------------------------------------------------------------
+
+
+def sub_steps(sysm: ShearletSystem) -> List[int]:
+    """Lattice step of every subband. Reading: the sampling matrix of scale j keeps
+    (2^(J-1-j) Z)^2, the finest scale every point, the lowpass (2^(J-1) Z)^2: each
+    subband at the rate its passband allows."""
+    J = sysm.n_scales
+    return [2 ** (J - 1) if m.scale < 0 else 2 ** max(0, J - 1 - m.scale) for m in sysm.meta]
+
+
+def forward_sub(x: np.ndarray, sysm: ShearletSystem, steps: Optional[Sequence[int]] = None
+                ) -> List[np.ndarray]:
+    """C_j sampled on its lattice: [C_j[::s_j, ::s_j] for every j] (2D)."""
+    steps = sub_steps(sysm) if steps is None else steps
+    C = forward(x, sysm)
+    return [C[j][::steps[j], ::steps[j]].copy() for j in range(sysm.R)]
+
+
+def adjoint_sub(c: Sequence[np.ndarray], sysm: ShearletSystem,
+                steps: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Adjoint of forward_sub: each subband's lattice values put back on the grid
+    (zeros elsewhere), then the adjoint of the full transform."""
+    steps = sub_steps(sysm) if steps is None else steps
+    full = np.zeros((sysm.R,) + tuple(sysm.dims))
+    for j in range(sysm.R):
+        full[j][::steps[j], ::steps[j]] = c[j]
+    return adjoint(full, sysm)
+
+
+def sub_frame_weight(sysm: ShearletSystem, steps: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Psi_sub = sum_j |psi_hat_j|^2 / s_j^2: the frame weight (eq. frame_filter) with
+    each subband's sampling density; the preconditioner's symbol."""
+    steps = sub_steps(sysm) if steps is None else steps
+    return sum(sysm.psi_hat(j) ** 2 / float(steps[j]) ** 2 for j in range(sysm.R))
+
+
+def cg_inverse_sub(c: Sequence[np.ndarray], sysm: ShearletSystem, iterations: int,
+                   precondition: bool = True, steps: Optional[Sequence[int]] = None
+                   ) -> Tuple[np.ndarray, List[float]]:
+    """Solve S x = T_sub* c, S = T_sub* T_sub, by (preconditioned) conjugate gradients
+    from x = 0 for `iterations` steps; returns x and the relative residual after each
+    step. The preconditioner (our addition) is the diagonal-in-frequency operator
+    v -> IFFT(FFT(v) / Psi_sub)."""
+    steps = sub_steps(sysm) if steps is None else steps
+
+    def S(v):
+        return adjoint_sub(forward_sub(v, sysm, steps), sysm, steps)
+    W = sub_frame_weight(sysm, steps)
+
+    def Pinv(v):
+        return np.real(_dft.ifftn(_dft.fftn(v) / W)) if precondition else v
+    b = adjoint_sub(c, sysm, steps)
+    nb = float(np.sqrt(np.sum(b * b)))
+    x = np.zeros(sysm.dims)
+    r = b.copy()
+    z = Pinv(r)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    hist = []
+    for _ in range(int(iterations)):
+        q = S(p)
+        alpha = rz / float(np.sum(p * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        z = Pinv(r)
+        rz_new = float(np.sum(r * z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        hist.append(float(np.sqrt(np.sum(r * r))) / nb)
+    return x, hist
+
+
 def thresholds(sysm: ShearletSystem, sigma: float, K: Sequence[float]) -> np.ndarray:
     """delta_j = K_{s(j)} sigma ||psi_j||_2 (Sec. 5.3 uses delta_j = K_j sigma; the
     factor ||psi_j||_2, the noise standard deviation in subband j, is the reading).

@@ -324,9 +324,17 @@ struct RowArgs {
   int n_rows;             // rows per slot (even) = n0
   TileMap tm;             // layout of the spectra (L0 = n0, TC of the pencil pass)
   float scale;            // ROW_C2R / ROW_RT: factor on the real output
-  int use_thr;
-  Thresholds thr;         // per slot: keep |c| >= thr (ROW_C2R / ROW_RT)
+  int use_thr;            // 0: none; 1: hard threshold; 2 (ROW_RT): lattice mask
+  Thresholds thr;         // per slot: keep |c| >= thr, or (use_thr == 2) keep the
+                          // points whose row and column are multiples of thr (a power
+                          // of two), the sampling lattice of a subsampled subband
 };
+
+// Lattice mask of the subsampled transform: keep (row, col) iff both are multiples of
+// the power of two s.
+__device__ __forceinline__ bool on_lattice(int row, int col, int s) {
+  return ((row | col) & (s - 1)) == 0;
+}
 
 // Row passes along the last axis (length L = n1), two real rows per complex line:
 //   ROW_R2C  real rows -> half spectra (unnormalised forward DFT)
@@ -389,7 +397,11 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A) k_row(RowArgs p) {
 #pragma unroll
       for (int ka = 0; ka < A; ++ka) {
         float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
-        if (p.use_thr) {
+        if (p.use_thr == 2) {  // rows 2 pr2, 2 pr2 + 1, column kb2 + B ka
+          const int st = (int)thr, k = kb2 + B * ka;
+          if (!on_lattice(2 * pr2, k, st)) c0 = 0.f;
+          if (!on_lattice(2 * pr2 + 1, k, st)) c1 = 0.f;
+        } else if (p.use_thr) {
           if (fabsf(c0) < thr) c0 = 0.f;
           if (fabsf(c1) < thr) c1 = 0.f;
         }
@@ -587,7 +599,17 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) res[aa] = sm[line2 * LS + kb2 * (A + 1) + aa];
         Dft<A, 1>::run(res);
-        if (p.use_thr) {  // uniform branch: no per-value predication when unused
+        if (p.use_thr == 2) {  // lattice mask: rows r0 + 2 line2 (+1), column kb2 + B ka
+          const int st = (int)thr, ra = r0 + 2 * line2;
+#pragma unroll
+          for (int ka = 0; ka < A; ++ka) {
+            const int k = kb2 + B * ka;
+            float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
+            if (!on_lattice(ra, k, st)) c0 = 0.f;
+            if (!on_lattice(ra + 1, k, st)) c1 = 0.f;
+            res[ka] = make_float2(c0, c1);
+          }
+        } else if (p.use_thr) {  // uniform branch: no per-value predication when unused
 #pragma unroll
           for (int ka = 0; ka < A; ++ka) {
             float c0 = res[ka].x * p.scale, c1 = res[ka].y * p.scale;
@@ -889,6 +911,99 @@ __global__ void __launch_bounds__(256) k_sub(const float* __restrict__ a, const 
       for (int64_t k = e; k < n; ++k) out[k] = a[k] - b[k];
     }
   }
+}
+
+// ------------------------------------------------- subsampled transform ---
+// Compact layout of subsampled coefficients: subband j keeps the points of the lattice
+// (s_j Z)^2 of its [n0][n1] plane, row-major [n0 / s_j][n1 / s_j], at offset off[j].
+
+struct SubPlan {
+  const int* step;       // [R] lattice step s_j (a power of two)
+  const int64_t* off;    // [R + 1] offsets into the compact array
+};
+
+// compact[off[j] + (i0 / s) (n1 / s) + i1 / s] = planes[j][i0][i1] on the lattice
+// (GATHER), or planes[j] = 0 off the lattice and the compact value on it (SCATTER).
+// blockIdx.y = j; threads stride over the plane's points.
+template <bool GATHER>
+__global__ void __launch_bounds__(256) k_sub_move(float* planes, float* compact, SubPlan sp,
+                                                  int n0, int n1) {
+  const int j = blockIdx.y, s = sp.step[j];
+  const int64_t N = (int64_t)n0 * n1;
+  float* pl = planes + (int64_t)j * N;
+  float* cp = compact + sp.off[j];
+  const int m1 = n1 / s;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(e / n1), i1 = (int)(e % n1);
+    const bool on = on_lattice(i0, i1, s);
+    if constexpr (GATHER) {
+      if (on) cp[(int64_t)(i0 / s) * m1 + i1 / s] = pl[e];
+    } else {
+      pl[e] = on ? cp[(int64_t)(i0 / s) * m1 + i1 / s] : 0.f;
+    }
+  }
+}
+
+// Deterministic FP64 dot product, stage 1: block b writes the sum of a[i] b[i] over its
+// grid-stride indices (fixed order) to part[b].
+__global__ void __launch_bounds__(256) k_dot_partial(const float* __restrict__ a,
+                                                     const float* __restrict__ b, int64_t n,
+                                                     double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)a[i] * (double)b[i];
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Stage 2 (one block of 256): out = sum of part[0, nparts) in a fixed order.
+__global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ part, int nparts,
+                                                   double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 256) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// Conjugate-gradient updates with the step sizes read from device scalars (no host
+// round trip): alpha = num / den; x += alpha p; r -= alpha q (q = S p).
+__global__ void __launch_bounds__(256) k_cg_xr(float* __restrict__ x, float* __restrict__ r,
+                                               const float* __restrict__ p,
+                                               const float* __restrict__ q,
+                                               const double* __restrict__ num,
+                                               const double* __restrict__ den, int64_t n) {
+  const double d = *den;
+  const float alpha = d != 0.0 ? (float)(*num / d) : 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    r[i] = fmaf(-alpha, q[i], r[i]);
+  }
+}
+
+// p = z + beta p with beta = num / den (den the previous iteration's num).
+__global__ void __launch_bounds__(256) k_cg_p(float* __restrict__ p, const float* __restrict__ z,
+                                              const double* __restrict__ num,
+                                              const double* __restrict__ den, int64_t n) {
+  const double d = *den;
+  const float beta = d != 0.0 ? (float)(*num / d) : 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(beta, p[i], z[i]);
 }
 
 }  // namespace dev

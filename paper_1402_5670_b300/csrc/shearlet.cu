@@ -551,6 +551,17 @@ struct sl_bank {
   float2* xhat_cl = nullptr;  // [TOTAL]
   float2* part_cl = nullptr;  // [ncl][TOTAL]
   float* inp_u = nullptr;     // sl_inpaint's iterate input (allocated on first use)
+  // subsampled transform (allocated on first use): lattice steps and compact offsets,
+  // a full coefficient stack, the conjugate-gradient vectors and scalars, and the
+  // preconditioner 1 / Psi_sub (FP64, tile-major)
+  std::vector<int> sub_step;
+  std::vector<int64_t> sub_off;
+  int* d_sub_step = nullptr;
+  int64_t* d_sub_off = nullptr;
+  float* sub_C = nullptr;     // [R][N]
+  float* cg = nullptr;        // [5][N]: x-free work vectors r, p, q, z, b
+  double* cg_dot = nullptr;   // [kDotParts] partial sums, then 8 scalars
+  double* invPsi_sub = nullptr;
   float* e2e_x = nullptr;     // sl_fwdinv_host buffers (allocated on first use)
   float* e2e_c = nullptr;
   cudaStream_t e2e_cap = nullptr;         // sl_fwdinv_host: capture stream, graph and the
@@ -571,6 +582,16 @@ static void free_device(sl_bank* b) {
   cudaFree(b->e2e_c);
   cudaFree(b->inp_u);
   b->inp_u = nullptr;
+  cudaFree(b->d_sub_step);
+  cudaFree(b->d_sub_off);
+  cudaFree(b->sub_C);
+  cudaFree(b->cg);
+  cudaFree(b->cg_dot);
+  cudaFree(b->invPsi_sub);
+  b->d_sub_step = nullptr;
+  b->d_sub_off = nullptr;
+  b->sub_C = b->cg = nullptr;
+  b->cg_dot = b->invPsi_sub = nullptr;
   if (b->e2e_graph) cudaGraphExecDestroy(b->e2e_graph);
   if (b->e2e_cap) cudaStreamDestroy(b->e2e_cap);
   b->e2e_graph = nullptr;
@@ -1076,11 +1097,11 @@ static sl_status spectrum_of(const Plan& P, const float* x, cudaStream_t st) {
 // address the plane of the group's first filter.
 template <int MODE>
 static sl_status slab_pass(const Plan& P, int nf, const float* creal_in, float* creal_out,
-                           const Thresholds* thr, cudaStream_t st) {
+                           const Thresholds* thr, cudaStream_t st, int thr_mode = 1) {
   RowArgs ra{};
   ra.scale = (float)(1.0 / (double)P.N);
   if (thr) {
-    ra.use_thr = 1;
+    ra.use_thr = thr_mode;
     ra.thr = *thr;
   }
   if (MODE == sl::dev::ROW_C2R) {
@@ -1263,7 +1284,142 @@ static sl_status denoise_plan(const Plan& P, const float* noisy, float* out, flo
   return inv_final(P, parts_used(P), true, out, st);
 }
 
-// ------------------------------------------------- cluster-fused orchestration ---
+// ---------------------------------------------------- subsampled transform ---
+// The subsampled digital shearlet transform (Def. digitSH_alpha with sampling
+// matrices): subband j is kept on the lattice (s_j Z)^2. Reading: s_j = 2^(J-1-j) for
+// scale j (coarse to fine, so the finest scale keeps every point) and 2^(J-1) for the
+// lowpass: each subband is sampled at the rate its passband allows. Its adjoint
+// scatters the lattice values back (zeros elsewhere). The inverse solves
+// S x = T_sub* c, S = T_sub* T_sub, by conjugate gradients (Sec. 3.4 and the frame
+// algorithms of Sec. 2.1), preconditioned with the diagonal (in frequency) operator
+// 1 / Psi_sub, Psi_sub = sum_j |psi_hat_j|^2 / s_j^2: the frame weight with each
+// subband's sampling density, which is exactly S when every s_j = 1.
+
+constexpr int kDotParts = 296;  // two blocks per SM of a B300
+
+static void sub_plan_of(const sl_bank* b, std::vector<int>* step, std::vector<int64_t>* off) {
+  const int J = b->spec.J;
+  step->assign(b->R, 1);
+  off->assign(b->R + 1, 0);
+  for (int j = 0; j < b->R; ++j) {
+    const int sc = b->filt[j].scale;
+    (*step)[j] = sc < 0 ? (1 << (J - 1)) : (1 << std::max(0, J - 1 - sc));
+    const int64_t sj = (*step)[j];
+    (*off)[j + 1] = (*off)[j] + (b->spec.dims[0] / sj) * (b->spec.dims[1] / sj);
+  }
+}
+
+static sl_status ensure_sub(sl_bank* b) {
+  if (b->spec.ndim != 2) return fail(SL_ENOTSUP, "the subsampled transform is 2D only");
+  if (b->cg) return SL_OK;
+  sub_plan_of(b, &b->sub_step, &b->sub_off);
+  for (int j = 0; j < b->R; ++j)
+    if (b->spec.dims[0] % b->sub_step[j] || b->spec.dims[1] % b->sub_step[j])
+      return fail(SL_ENOTSUP, "grid sides must be multiples of every lattice step 2^(J-1)");
+  const int64_t N = b->N, Nh = b->Nh;
+  // 1 / Psi_sub on the half spectrum, FP64, from the normalised filters
+  std::vector<double> acc((size_t)Nh, 0.0), f((size_t)Nh);
+  for (int j = 0; j < b->R; ++j) {
+    b->ev->eval(j, f.data());
+    const double w = b->scale * b->scale / ((double)b->sub_step[j] * b->sub_step[j]);
+    for (int64_t i = 0; i < Nh; ++i) acc[i] += w * f[i] * f[i];
+  }
+  for (int64_t i = 0; i < Nh; ++i) {
+    if (!(acc[i] > 0.0)) return fail(SL_EINVAL, "the subsampled frame weight vanishes");
+    acc[i] = 1.0 / acc[i];
+  }
+  std::vector<double> tiled((size_t)b->Nhp, 0.0);
+  tile_major(b, acc.data(), tiled.data());
+  auto bail = [&](const char* what) {
+    cudaGetLastError();
+    cudaFree(b->d_sub_step);
+    cudaFree(b->d_sub_off);
+    cudaFree(b->sub_C);
+    cudaFree(b->cg);
+    cudaFree(b->cg_dot);
+    cudaFree(b->invPsi_sub);
+    b->d_sub_step = nullptr;
+    b->d_sub_off = nullptr;
+    b->sub_C = b->cg = nullptr;
+    b->cg_dot = b->invPsi_sub = nullptr;
+    return fail(SL_ENOMEM, what);
+  };
+  if (cudaMalloc((void**)&b->d_sub_step, b->R * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_sub_off, (b->R + 1) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc((void**)&b->sub_C, (size_t)b->R * N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&b->cg_dot, (kDotParts + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&b->invPsi_sub, (size_t)b->Nhp * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&b->cg, 5 * (size_t)N * sizeof(float)) != cudaSuccess)
+    return bail("allocating the subsampled transform's buffers");
+  if (cudaMemcpy(b->d_sub_step, b->sub_step.data(), b->R * sizeof(int), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_sub_off, b->sub_off.data(), (b->R + 1) * sizeof(int64_t),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->invPsi_sub, tiled.data(), tiled.size() * sizeof(double),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail("uploading the subsampled transform's tables");
+  return SL_OK;
+}
+
+static sl_status sub_move(const sl_bank* b, bool gather, float* planes, float* compact,
+                          cudaStream_t st) {
+  sl::dev::SubPlan sp{b->d_sub_step, b->d_sub_off};
+  const int n0 = (int)b->spec.dims[0], n1 = (int)b->spec.dims[1];
+  dim3 grid((unsigned)std::min<int64_t>((b->N + 255) / 256, 64), (unsigned)b->R);
+  return launched(timed_launch(gather ? "sub_gather" : "sub_scatter", st, [&]() {
+                    if (gather)
+                      sl::dev::k_sub_move<true><<<grid, 256, 0, st>>>(planes, compact, sp, n0, n1);
+                    else
+                      sl::dev::k_sub_move<false><<<grid, 256, 0, st>>>(planes, compact, sp, n0, n1);
+                  }),
+                  "subsample move");
+}
+
+// *out = <a, b> over n floats, FP64, deterministic.
+static sl_status dot(const sl_bank* b, const float* x, const float* y, double* out,
+                     cudaStream_t st) {
+  const int64_t n = b->N;
+  double* part = b->cg_dot;
+  SL_TRY(launched(timed_launch("cg_dot", st, [&]() {
+                    sl::dev::k_dot_partial<<<kDotParts, 256, 0, st>>>(x, y, n, part);
+                    sl::dev::k_dot_final<<<1, 256, 0, st>>>(part, kDotParts, out);
+                  }),
+                  "cg_dot"));
+  return SL_OK;
+}
+
+// q = S p = T_sub* T_sub p: one fused pass (forward, lattice mask, adjoint) with the
+// coefficients never leaving the chip.
+static sl_status sub_frame_op(const Plan& P, const float* p, float* q, cudaStream_t st) {
+  const sl_bank* b = P.bank;
+  SL_TRY(spectrum_of(P, p, st));
+  for (int g = 0; g < P.ngroups; ++g) {
+    const int j0 = g * P.G;
+    const int nf = std::min(P.G, P.R - j0);
+    Thresholds t;
+    for (int i = 0; i < nf; ++i) t.v[i] = (float)b->sub_step[j0 + i];
+    SL_TRY(fwd_filter_pass(P, j0, nf, st));
+    SL_TRY(slab_pass<sl::dev::ROW_RT>(P, nf, nullptr, nullptr, &t, st, 2));
+    SL_TRY(inv_acc_pass(P, g, j0, nf, st));
+  }
+  return inv_final(P, parts_used(P), false, q, st);
+}
+
+// z = IFFT(FFT(r) / Psi_sub): the preconditioner.
+static sl_status sub_precondition(const Plan& P, const float* r, float* z, cudaStream_t st) {
+  SL_TRY(spectrum_of(P, r, st));
+  const int64_t n = P.Nhp;
+  const int grid = (int)std::min<int64_t>((n / 2 + 255) / 256, 4 * 148);
+  const double* w = P.bank->invPsi_sub;
+  float2* xh = P.xhat;
+  SL_TRY(launched(timed_launch("cg_precondition", st, [&]() {
+                    sl::dev::k_reduce_parts<<<grid, 256, 0, st>>>(xh, 1, n, w, xh, n);
+                  }),
+                  "cg_precondition"));
+  return spectrum_to_signal(P, z, st);
+}
+
+// ------------------------------------------------- cluster-fused orchestration ---// ------------------------------------------------- cluster-fused orchestration ---
 
 // x -> spectrum (one cluster) -> per filter C2R (all clusters).
 static sl_status cl_forward(const sl_bank* b, const float* x, float* coeffs, cudaStream_t st) {
@@ -1401,6 +1557,91 @@ sl_status sl_inverse_finish(const sl_bank* b, const float* summed, int dual, flo
   Plan P = plan_of(b);
   return parts_to_signal(P, reinterpret_cast<const float2*>(summed), 1, dual != 0, x,
                          (cudaStream_t)stream);
+}
+
+sl_status sl_sub_layout(const sl_bank* b, int* step, int64_t* offset) {
+  if (!b) return fail(SL_EINVAL, "bank is NULL");
+  if (b->spec.ndim != 2) return fail(SL_ENOTSUP, "the subsampled transform is 2D only");
+  std::vector<int> st;
+  std::vector<int64_t> off;
+  sub_plan_of(b, &st, &off);
+  if (step) std::copy(st.begin(), st.end(), step);
+  if (offset) std::copy(off.begin(), off.end(), offset);
+  return SL_OK;
+}
+
+sl_status sl_forward_sub(const sl_bank* cb, const float* x, float* coeffs_sub, void* stream) {
+  SL_TRY(check_call(cb));
+  if (!x || !coeffs_sub) return fail(SL_EINVAL, "x or coeffs_sub is NULL");
+  SL_TRY(check_aligned(x, x));
+  sl_bank* b = const_cast<sl_bank*>(cb);
+  SL_TRY(ensure_sub(b));
+  cudaStream_t st = (cudaStream_t)stream;
+  SL_TRY(forward_plan(plan_of(b), x, b->sub_C, st));
+  return sub_move(b, true, b->sub_C, coeffs_sub, st);
+}
+
+sl_status sl_adjoint_sub(const sl_bank* cb, const float* coeffs_sub, float* x, void* stream) {
+  SL_TRY(check_call(cb));
+  if (!x || !coeffs_sub) return fail(SL_EINVAL, "x or coeffs_sub is NULL");
+  SL_TRY(check_aligned(x, x));
+  sl_bank* b = const_cast<sl_bank*>(cb);
+  SL_TRY(ensure_sub(b));
+  cudaStream_t st = (cudaStream_t)stream;
+  SL_TRY(sub_move(b, false, b->sub_C, const_cast<float*>(coeffs_sub), st));
+  return backward(plan_of(b), b->sub_C, x, false, st);
+}
+
+sl_status sl_inverse_sub(const sl_bank* cb, const float* coeffs_sub, float* x, int iterations,
+                         int precondition, double* rel_residual, void* stream) {
+  SL_TRY(check_call(cb));
+  if (!x || !coeffs_sub) return fail(SL_EINVAL, "x or coeffs_sub is NULL");
+  SL_TRY(check_aligned(x, x));
+  if (iterations < 0) return fail(SL_EINVAL, "iterations must be >= 0");
+  sl_bank* b = const_cast<sl_bank*>(cb);
+  SL_TRY(ensure_sub(b));
+  cudaStream_t st = (cudaStream_t)stream;
+  const Plan P = plan_of(b);
+  const int64_t N = b->N;
+  float* r = b->cg;
+  float* p = b->cg + N;
+  float* q = b->cg + 2 * N;
+  float* z = precondition ? b->cg + 3 * N : r;
+  float* rhs = b->cg + 4 * N;
+  double* sc = b->cg_dot + kDotParts;  // [0], [1]: <r, z> of alternate iterations; [2]: <p, q>
+  const int grid = (int)std::min<int64_t>((N + 255) / 256, 4 * 148);
+  // rhs = T_sub* c; x = 0, r = rhs, z = P^-1 r, p = z
+  SL_TRY(sl_adjoint_sub(b, coeffs_sub, rhs, stream));
+  SL_CUDA(cudaMemsetAsync(x, 0, (size_t)N * sizeof(float), st));
+  SL_CUDA(cudaMemcpyAsync(r, rhs, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (precondition) SL_TRY(sub_precondition(P, r, z, st));
+  SL_CUDA(cudaMemcpyAsync(p, z, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  SL_TRY(dot(b, r, z, sc + 0, st));
+  for (int it = 0; it < iterations; ++it) {
+    double* rz_old = sc + (it & 1);
+    double* rz_new = sc + ((it + 1) & 1);
+    SL_TRY(sub_frame_op(P, p, q, st));
+    SL_TRY(dot(b, p, q, sc + 2, st));
+    SL_TRY(launched(timed_launch("cg_update", st, [&]() {
+                      sl::dev::k_cg_xr<<<grid, 256, 0, st>>>(x, r, p, q, rz_old, sc + 2, N);
+                    }),
+                    "cg_update"));
+    if (precondition) SL_TRY(sub_precondition(P, r, z, st));
+    SL_TRY(dot(b, r, z, rz_new, st));
+    SL_TRY(launched(timed_launch("cg_update", st, [&]() {
+                      sl::dev::k_cg_p<<<grid, 256, 0, st>>>(p, z, rz_new, rz_old, N);
+                    }),
+                    "cg_update"));
+  }
+  if (rel_residual) {
+    SL_TRY(dot(b, r, r, sc + 3, st));
+    SL_TRY(dot(b, rhs, rhs, sc + 4, st));
+    double h[2] = {0.0, 0.0};
+    SL_CUDA(cudaMemcpyAsync(h, sc + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SL_CUDA(cudaStreamSynchronize(st));
+    *rel_residual = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  }
+  return SL_OK;
 }
 
 sl_status sl_threshold(const sl_bank* b, float* coeffs, float sigma, const float* K,

@@ -60,6 +60,10 @@ SIGNATURES = {
     "sl_fwdinv_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sl_forward_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sl_spectrum_points": (ctypes.c_int, [_vp, _c_int64_p]),
+    "sl_sub_layout": (ctypes.c_int, [_vp, _c_int_p, _c_int64_p]),
+    "sl_forward_sub": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_adjoint_sub": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sl_inverse_sub": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _c_double_p, _vp]),
     "sl_spectrum": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sl_forward_range": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "sl_inverse_partial": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
@@ -464,6 +468,44 @@ class Bank:
         sl_inverse_finish(self.handle, _dev_ptr(summed, "summed", 2 * self.spectrum_points), dual,
                           _dev_ptr(out, "x", self.N), _stream_ptr(stream))
         return out
+
+    # -------- subsampled transform (2D) --------
+
+    def sub_layout(self):
+        """(steps [R], offsets [R + 1]) of the subsampled transform's compact layout."""
+        st = np.zeros(self.R, dtype=np.int32)
+        off = np.zeros(self.R + 1, dtype=np.int64)
+        _check(lib().sl_sub_layout(self.handle, st.ctypes.data_as(_c_int_p),
+                                   off.ctypes.data_as(_c_int64_p)), "sl_sub_layout")
+        return st, off
+
+    def forward_sub(self, x, out=None, stream=None):
+        n = int(self.sub_layout()[1][-1])
+        out = self._empty((n,)) if out is None else out
+        _check(lib().sl_forward_sub(self.handle, _dev_ptr(x, "x", self.N),
+                                    _dev_ptr(out, "coeffs_sub", n), _stream_ptr(stream)),
+               "sl_forward_sub")
+        return out
+
+    def adjoint_sub(self, coeffs_sub, out=None, stream=None):
+        n = int(self.sub_layout()[1][-1])
+        out = self._empty(self.dims) if out is None else out
+        _check(lib().sl_adjoint_sub(self.handle, _dev_ptr(coeffs_sub, "coeffs_sub", n),
+                                    _dev_ptr(out, "x", self.N), _stream_ptr(stream)),
+               "sl_adjoint_sub")
+        return out
+
+    def inverse_sub(self, coeffs_sub, iterations: int, precondition: bool = True, out=None,
+                    stream=None):
+        """(x, relative residual) after `iterations` conjugate-gradient steps."""
+        n = int(self.sub_layout()[1][-1])
+        out = self._empty(self.dims) if out is None else out
+        res = ctypes.c_double()
+        _check(lib().sl_inverse_sub(self.handle, _dev_ptr(coeffs_sub, "coeffs_sub", n),
+                                    _dev_ptr(out, "x", self.N), int(iterations),
+                                    int(bool(precondition)), ctypes.byref(res),
+                                    _stream_ptr(stream)), "sl_inverse_sub")
+        return out, res.value
 
     def threshold_(self, coeffs, sigma: float, K: Sequence[float], stream=None):
         self._check_K(K)
