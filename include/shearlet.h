@@ -299,6 +299,14 @@ sl_status sl_adjoint_sub(const sl_bank* bank, const float* coeffs_sub, float* x,
 sl_status sl_inverse_sub(const sl_bank* bank, const float* coeffs_sub, float* x, int iterations,
                          int precondition, double* rel_residual, void* stream);
 
+/* Synchronises `stream` and reports whether a bounded wait of a transform kernel on
+ * the current device ran out since the last check: the filter-loop kernels stage
+ * their tiles with bulk copies that complete on shared-memory barriers, and every
+ * wait on those gives up after about two seconds, sets a device flag and returns
+ * with that CTA's work undone. SL_ETIMEOUT (and the flag cleared) if so, SL_OK
+ * otherwise. */
+sl_status sl_device_check(void* stream);
+
 /*
  * Hard thresholding in place (eq. hard_tresholding, Sec. 5.3): for every filter
  * j >= 1, C_j(m) = 0 unless |C_j(m)| >= K[scale(j)] * sigma * ||psi_j||_2. The lowpass

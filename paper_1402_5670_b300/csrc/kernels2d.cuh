@@ -195,6 +195,91 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------------ bulk copies (TMA engine) ---
+// Stages of the filter-loop kernels are filled by cp.async.bulk copies that complete
+// on one mbarrier per stage (transaction bytes); one thread (or the lanes of warp 0)
+// issues them, so the transform warps spend no issue slots on copy loops. Every wait
+// is bounded: a wait that runs out sets g_sl_wait_error (reported by sl_device_check)
+// and the kernel returns after a bounded drain of its copies in flight.
+
+__device__ int g_sl_wait_error;  // 0, or 1 once a bounded wait ran out
+
+constexpr long long kWaitCycles = 4000000000LL;  // about two seconds of SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Arrive on the barrier (the one expected arrival) and announce `bytes` of copies.
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+// Order this thread's earlier generic-proxy accesses of shared memory before the
+// bulk copies it issues next (the stage being refilled was just read).
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Global -> shared bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned), completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for the phase of the given parity; false once kWaitCycles pass without it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+// Two-stage ring of a persistent kernel: fill i goes to stage i & 1 and completes
+// phase (i >> 1) & 1 of that stage's barrier; fills and waits happen in this order,
+// and a stage is refilled only after it was waited on and consumed. The counters are
+// CTA-uniform (the loops are).
+struct BulkRing {
+  uint64_t* bar;    // [2] in shared memory
+  int issued = 0;   // fills issued
+  int waited = 0;   // fills waited for
+  // Wait for the next fill; CTA-uniform result (includes a CTA barrier).
+  __device__ __forceinline__ bool wait() {
+    const int i = waited++;
+    const bool ok = mbar_wait_bounded(bar + (i & 1), (uint32_t)((i >> 1) & 1));
+    return !__syncthreads_or(!ok);
+  }
+  // After a wait ran out: flag it, and let the fills still in flight (the one waited
+  // for and any later one) land, each wait bounded again, before the CTA exits.
+  __device__ __forceinline__ void abandon() {
+    if (threadIdx.x == 0) {
+      atomicExch(&g_sl_wait_error, 1);
+      for (int i = waited - 1; i < issued; ++i)
+        mbar_wait_bounded(bar + (i & 1), (uint32_t)((i >> 1) & 1));
+    }
+    __syncthreads();
+  }
+};
+
 // Copy `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
 // shared memory with every thread of the CTA issuing 16-byte asynchronous copies.
 template <int T>
@@ -206,33 +291,46 @@ __device__ __forceinline__ void cp_async_block(void* dst, const void* src, int b
 
 // Forward filter pass as a persistent, software-pipelined kernel: work item i is
 // (tile i / nfilt, filter j0 + i % nfilt); CTA c takes items c, c + gridDim.x, ...
-// While item k is transformed, the signal and filter tiles of item k + 1 stream into
-// the other shared-memory stage with cp.async, so global-memory latency overlaps
-// with the FFT. Output as COL_FWD_FILT: out[s] = IFFT_0(in * psi[j0 + s]).
+// While item k is transformed, the signal and filter tiles of item k + 1 (two
+// contiguous blocks of the tile-major layout) land in the other shared-memory stage
+// by bulk copies, so global-memory latency overlaps with the FFT.
+// Output as COL_FWD_FILT: out[s] = IFFT_0(in * psi[j0 + s]).
 template <int L>
 __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLF) k_col_fwd_pipe(ColArgs p) {
   using G = Geo<L>;
-  constexpr int A = G::A, B = G::B, TC = G::TC, T = G::T, XS = G::XS;
+  constexpr int A = G::A, B = G::B, TC = G::TC, XS = G::XS;
   constexpr int TILE = L * TC;  // elements of one tile
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* xs = reinterpret_cast<float2*>(smraw);                 // [2][TILE]
   float* ps = reinterpret_cast<float*>(xs + 2 * TILE);           // [2][TILE]
   float2* ex = reinterpret_cast<float2*>(ps + 2 * TILE);         // [B][XS]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ex + B * XS);     // [2]
   const int tid = threadIdx.x;
   const float2* tw = g_twiddle + twiddle_offset(L);
   const int nitems = (int)(p.Nhp / TILE) * p.nfilt;  // tiles x filters
   const int line = tid % TC, a = tid / TC;
   const int line2 = tid % TC, kb2 = tid / TC;
   const bool in2 = tid < TC * B;
+  if (tid == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  BulkRing ring{bars};
 
   auto issue = [&](int item, int stage) {
     if (item < nitems) {
-      const int tile = item / p.nfilt, j = p.j0 + item % p.nfilt;
-      cp_async_block<T>(xs + stage * TILE, p.in + (int64_t)tile * TILE, TILE * 8);
-      cp_async_block<T>(ps + stage * TILE, p.psi + (int64_t)j * p.Nhp + (int64_t)tile * TILE,
-                        TILE * 4);
+      if (tid == 0) {
+        const int tile = item / p.nfilt, j = p.j0 + item % p.nfilt;
+        fence_proxy_async();
+        mbar_expect(bars + stage, TILE * 12);
+        bulk_g2s(xs + stage * TILE, p.in + (int64_t)tile * TILE, TILE * 8, bars + stage);
+        bulk_g2s(ps + stage * TILE, p.psi + (int64_t)j * p.Nhp + (int64_t)tile * TILE, TILE * 4,
+                 bars + stage);
+      }
+      ++ring.issued;
     }
-    cp_async_commit();
   };
 
   float2 twr[B];  // this thread's inter-pass twiddles, the same for every item
@@ -244,8 +342,10 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLF) k_col_fwd_pipe(ColArg
   issue(item + gridDim.x, 1);
   for (int k = 0; item < nitems; ++k, item += gridDim.x) {
     const int stage = k & 1;
-    cp_async_wait<1>();
-    __syncthreads();
+    if (!ring.wait()) {  // stage filled; previous item's exchange reads done
+      ring.abandon();
+      return;
+    }
     const int tile = item / p.nfilt, s = item % p.nfilt;
     float2 v[B];
 #pragma unroll
@@ -270,12 +370,11 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLF) k_col_fwd_pipe(ColArg
       for (int ka = 0; ka < A; ++ka) o[(kb2 + B * ka) * TC + line2] = w[ka];
     }
   }
-  cp_async_wait<0>();
 }
 
 template <int L>
-constexpr int col_pipe_smem_bytes() {
-  return 2 * L * Geo<L>::TC * (8 + 4) + Geo<L>::B * Geo<L>::XS * 8;
+constexpr int col_pipe_smem_bytes() {  // two stages, the exchange, two mbarriers
+  return 2 * L * Geo<L>::TC * (8 + 4) + Geo<L>::B * Geo<L>::XS * 8 + 16;
 }
 
 // out[e] = (sum_q parts[q][e]) * w[e] (w in FP64, or 1 when w == nullptr), over one
@@ -507,6 +606,7 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char* stg = smraw;                                        // [2][stage_bytes]
   float2* sm = reinterpret_cast<float2*>(smraw + 2 * stage_bytes);  // exchange
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + 2 * stage_bytes + RP::XB);  // [2]
   const int tid = threadIdx.x;
   const float2* tw = g_twiddle + twiddle_offset(L);
   const TileMap tm = p.tm;
@@ -517,14 +617,31 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
   const bool in2 = tid < PAIRS * B;
   const int nrun = NPp / tm_tc(tm);  // tile runs per row
 
+  // Stage layouts. R2C: the item's 2 PAIRS real rows, contiguous: one bulk copy,
+  // completing on the stage's mbarrier. C2R / RT: the item's rows gathered from every
+  // pencil tile (runs of TC elements) by 16-byte cp.async copies of all threads into
+  // [row][NPp] (one bulk copy per run measured slower: 65 copies of 256 bytes per item
+  // at 512^2).
+  if (MODE == ROW_R2C && tid == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  BulkRing ring{bars};
+
   auto issue = [&](int item, int stage) {
     if (item < nitems) {
       const int slot = item / groups, r0 = (item % groups) * 2 * PAIRS;
       unsigned char* dst = stg + stage * stage_bytes;
       if constexpr (MODE == ROW_R2C) {
-        const float* src = p.in_real + (int64_t)slot * p.in_stride + (int64_t)r0 * L;
-        for (int o = tid * 16; o < 2 * PAIRS * L * 4; o += T * 16)
-          cp_async16(dst + o, reinterpret_cast<const char*>(src) + o);
+        if (tid == 0) {
+          const float* src = p.in_real + (int64_t)slot * p.in_stride + (int64_t)r0 * L;
+          fence_proxy_async();
+          mbar_expect(bars + stage, 2 * PAIRS * L * 4);
+          bulk_g2s(dst, src, 2 * PAIRS * L * 4, bars + stage);
+        }
+        ++ring.issued;
       } else {
         const float2* src = p.in_half + (int64_t)slot * p.in_stride;
         // tile run t of row r0 + rr is TC = 2^lg elements at ((t L0 + r0 + rr) << lg):
@@ -542,7 +659,17 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
         }
       }
     }
-    cp_async_commit();
+    if constexpr (MODE != ROW_R2C) cp_async_commit();
+  };
+  // wait for item k's stage (CTA-uniform; includes a CTA barrier)
+  auto wait_stage = [&]() -> bool {
+    if constexpr (MODE == ROW_R2C) {
+      return ring.wait();
+    } else {
+      cp_async_wait<1>();
+      __syncthreads();
+      return true;
+    }
   };
 
   // this thread's inter-pass twiddles are the same for every item
@@ -556,8 +683,10 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
   for (int k = 0; item < nitems; ++k, item += gridDim.x) {
     const int stage = k & 1;
     const int slot = item / groups, r0 = (item % groups) * 2 * PAIRS;
-    cp_async_wait<1>();
-    __syncthreads();
+    if (!wait_stage()) {  // stage filled; previous item's exchange reads done
+      ring.abandon();
+      return;
+    }
     float2 res[A];
     if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
       const float2* in = reinterpret_cast<const float2*>(stg + stage * stage_bytes);
@@ -692,22 +821,23 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
     }
     __syncthreads();  // exchange reused by the next item
   }
-  cp_async_wait<0>();
+  if constexpr (MODE != ROW_R2C) cp_async_wait<0>();
 }
 
 // Inverse filter pass (COL_INV_ACC) as a persistent pipelined kernel: work item i is
 // (tile i % ntiles, split i / ntiles); the CTA streams the (Z_j tile, psi_j tile)
-// pairs of its items' filters through two shared-memory stages and accumulates
-// psi_j * FFT_0(Z_j) in registers, writing one partial per item.
+// pairs of its items' filters through two shared-memory stages (bulk copies) and
+// accumulates psi_j * FFT_0(Z_j) in registers, writing one partial per item.
 template <int L>
 __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLI) k_col_inv_pipe(ColArgs p) {
   using G = Geo<L>;
-  constexpr int A = G::A, B = G::B, TC = G::TC, T = G::T, XS = G::XS;
+  constexpr int A = G::A, B = G::B, TC = G::TC, XS = G::XS;
   constexpr int TILE = L * TC;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* zs = reinterpret_cast<float2*>(smraw);        // [2][TILE]
   float* ps = reinterpret_cast<float*>(zs + 2 * TILE);  // [2][TILE]
   float2* ex = reinterpret_cast<float2*>(ps + 2 * TILE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ex + B * XS);  // [2]
   const int tid = threadIdx.x;
   const float2* tw = g_twiddle + twiddle_offset(L);
   const int ntiles = (int)(p.Nhp / TILE);
@@ -716,18 +846,30 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLI) k_col_inv_pipe(ColArg
   const int line = tid % TC, a = tid / TC;
   const int line2 = tid % TC, kb2 = tid / TC;
   const bool in2 = tid < TC * B;
+  if (tid == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  BulkRing ring{bars};
 
   // the CTA's load sequence: (item, filter) pairs in order
   auto first_filter = [&](int item) { return (item / ntiles) * p.fps; };
   auto last_filter = [&](int item) { return min(first_filter(item) + p.fps, p.nfilt); };
   auto issue = [&](int item, int f, int stage) {
     if (item < nitems) {
-      const int tile = item % ntiles;
-      cp_async_block<T>(zs + stage * TILE, p.in + (int64_t)f * p.Nhp + (int64_t)tile * TILE, TILE * 8);
-      cp_async_block<T>(ps + stage * TILE, p.psi + (int64_t)(p.j0 + f) * p.Nhp + (int64_t)tile * TILE,
-                        TILE * 4);
+      if (tid == 0) {
+        const int tile = item % ntiles;
+        fence_proxy_async();
+        mbar_expect(bars + stage, TILE * 12);
+        bulk_g2s(zs + stage * TILE, p.in + (int64_t)f * p.Nhp + (int64_t)tile * TILE, TILE * 8,
+                 bars + stage);
+        bulk_g2s(ps + stage * TILE, p.psi + (int64_t)(p.j0 + f) * p.Nhp + (int64_t)tile * TILE,
+                 TILE * 4, bars + stage);
+      }
+      ++ring.issued;
     }
-    cp_async_commit();
   };
   auto advance = [&](int& item, int& f) {
     if (++f >= last_filter(item)) {
@@ -747,8 +889,10 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLI) k_col_inv_pipe(ColArg
   for (int i = 0; i < A; ++i) acc[i] = make_float2(0.f, 0.f);
   for (int k = 0; cur_item < nitems; ++k) {
     const int stage = k & 1;
-    cp_async_wait<1>();
-    __syncthreads();
+    if (!ring.wait()) {  // stage filled; previous exchange reads done
+      ring.abandon();
+      return;
+    }
     float2 v[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) v[b] = zs[stage * TILE + (a + A * b) * TC + line];
@@ -787,12 +931,11 @@ __global__ void __launch_bounds__(Geo<L>::T, SL_MINB_COLI) k_col_inv_pipe(ColArg
       }
     }
   }
-  cp_async_wait<0>();
 }
 
 template <int L>
-constexpr int col_inv_pipe_smem_bytes() {
-  return 2 * L * Geo<L>::TC * (8 + 4) + Geo<L>::B * Geo<L>::XS * 8;
+constexpr int col_inv_pipe_smem_bytes() {  // two stages, the exchange, two mbarriers
+  return 2 * L * Geo<L>::TC * (8 + 4) + Geo<L>::B * Geo<L>::XS * 8 + 16;
 }
 
 // ------------------------------------------------------------ elementwise ---

@@ -224,8 +224,9 @@ static cudaError_t launch_row_pipe_t(int slots, int L0, int NPp, cudaStream_t st
   constexpr int PAIRS = sl::dev::col_tile_of(L);
   constexpr int T = PAIRS * sl::dev::Split<L>::A;
   auto k = sl::dev::k_row_pipe<L, MODE, PAIRS>;
+  // two stages (the real rows, or the rows' half spectra), the exchange, two mbarriers
   const int stage = MODE == sl::dev::ROW_R2C ? 2 * PAIRS * L * 4 : 2 * PAIRS * NPp * 8;
-  const int smem = 2 * stage + sl::dev::RowPipe<L, MODE, PAIRS>::XB;
+  const int smem = 2 * stage + sl::dev::RowPipe<L, MODE, PAIRS>::XB + 16;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int items = slots * (L0 / (2 * PAIRS));
@@ -1640,6 +1641,22 @@ sl_status sl_inverse_sub(const sl_bank* cb, const float* coeffs_sub, float* x, i
     SL_CUDA(cudaMemcpyAsync(h, sc + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SL_CUDA(cudaStreamSynchronize(st));
     *rel_residual = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  }
+  return SL_OK;
+}
+
+sl_status sl_device_check(void* stream) {
+  int dev = -1;
+  SL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || !g_dev_init[dev]) return SL_OK;  // nothing ran here yet
+  SL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  SL_CUDA(cudaMemcpyFromSymbol(&h, sl::dev::g_sl_wait_error, sizeof(int)));
+  if (h) {
+    const int zero = 0;
+    SL_CUDA(cudaMemcpyToSymbol(sl::dev::g_sl_wait_error, &zero, sizeof(int)));
+    return fail(SL_ETIMEOUT, "a bounded wait for a bulk copy ran out in a transform kernel "
+                             "(its results are incomplete)");
   }
   return SL_OK;
 }

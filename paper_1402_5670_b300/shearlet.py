@@ -97,6 +97,7 @@ SIGNATURES = {
     "sl_mlp_set_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sl_mlp_check": (ctypes.c_int, [_vp, _vp]),
     "sl_error_stats": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _c_double_p, _vp]),
+    "sl_device_check": (ctypes.c_int, [_vp]),
     "sl_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "sl_profile_reset": (ctypes.c_int, []),
     "sl_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), _c_int64_p,
@@ -303,6 +304,11 @@ def sl_error_stats(y, ref, stream=None) -> dict:
             "sum_sq_ref": out[3], "rel_max": out[0] / max(out[1], 1e-300),
             "rel_l2": math.sqrt(out[2] / max(out[3], 1e-300)),
             "psnr": 20 * math.log10(255 * math.sqrt(n) / math.sqrt(max(out[2], 1e-300)))}
+
+
+def sl_device_check(stream=None) -> None:
+    """Synchronise and raise if a bounded wait of a transform kernel ran out."""
+    _check(lib().sl_device_check(_stream_ptr(stream)), "sl_device_check")
 
 
 def sl_profile_enable(on: bool) -> None:
