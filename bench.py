@@ -437,6 +437,18 @@ def extras(b, x, clean, C, flush, args):
         out["batched_uneven_64"] = batched_uneven(flush, steps, peak)
     except Exception as e:  # report, do not fail the headline line
         out["batched_uneven_64"] = {"error": str(e)}
+    try:
+        out["decomposition_512"] = decomposition_run(b, flush)
+    except Exception as e:  # report, do not fail the headline line
+        out["decomposition_512"] = {"error": str(e)}
+    try:
+        out["subsampled_cg"] = subsampled_run(b, x, flush, steps)
+    except Exception as e:  # report, do not fail the headline line
+        out["subsampled_cg"] = {"error": str(e)}
+    try:
+        out["filter_ranges_split"] = split_run(b, x, flush, steps)
+    except Exception as e:  # report, do not fail the headline line
+        out["filter_ranges_split"] = {"error": str(e)}
     # 3D volume, 128^3, three scales, levels (1,1,2): R = 292
     try:
         b3 = Bank((128, 128, 128), 3, (1, 1, 2), device=b.device)
@@ -563,61 +575,160 @@ def tc_vs_fp32(b, x, flush, steps: int, peak: float) -> dict:
     return res
 
 
+def decomposition_run(b, flush) -> dict:
+    """Image decomposition (Sec. 5.5) of a 512^2 curves + points image into its
+    curvilinear part (this shearlet bank) and isotropic part (a four-scale wavelet
+    bank): 100 iterations, delta 765 -> 1, device time of the whole call."""
+    import torch
+    from paper_1402_5670_b300 import synth
+    from paper_1402_5670_b300.shearlet import Bank
+    c, p = synth.points_and_curves(DIMS, SEED + 11)
+    f = torch.from_numpy(c + p).cuda()
+    W = Bank.wavelets(DIMS, J, device=b.device)
+    f0, f1 = b.decompose(W, f, 765.0, 1.0, 3)  # warm-up (allocates the work buffer)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    ev[0].record(st)
+    b.decompose(W, f, 765.0, 1.0, 100, out0=f0, out1=f1)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    res = float((f - f0 - f1).norm() / f.norm())
+    W.close()
+    return {"ms_total": ms, "iterations": 100, "ms_per_iteration": ms / 100,
+            "rel_residual": res, "R_shearlet": b.R, "R_wavelet": 1 + 3 * J,
+            "note": "each iteration: two elementwise passes and two fused denoising passes"}
+
+
+def subsampled_run(b, x, flush, steps: int) -> dict:
+    """The subsampled transform on the 512^2 image (subband j kept on the lattice
+    (2^(3-s(j)) Z)^2): forward time, and the conjugate-gradient inverse (10
+    preconditioned steps, 40 plain steps) with its reconstruction error."""
+    import torch
+    st_, off = b.sub_layout()
+    c = torch.empty(int(off[-1]), device="cuda")
+    ms_f = _time_graph(lambda: b.forward_sub(x, out=c), flush, steps)
+    y = torch.empty_like(x)
+    res = {}
+    for name, iters, pre in (("preconditioned", 10, True), ("plain", 40, False)):
+        b.inverse_sub(c, iters, pre, out=y)  # warm-up, allocation
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        _, r = b.inverse_sub(c, iters, pre, out=y)
+        e1.record(st)
+        torch.cuda.synchronize()
+        res[name] = {"iterations": iters, "ms": e0.elapsed_time(e1),
+                     "rel_residual": r,
+                     "rel_err_reconstruction": float((y - x).abs().max() / x.abs().max())}
+    return {"coefficients": int(off[-1]), "redundancy": int(off[-1]) / b.N,
+            "forward_ms": ms_f, "inverse": res}
+
+
+def split_run(b, x, flush, steps: int) -> dict:
+    """One transform split by filter ranges (the multi-GPU form), both ranges run on
+    this one GPU: spectrum, two forward ranges, two partial inverses, their sum and
+    the finish, against sl_forward + sl_inverse (no collective is timed here)."""
+    import torch
+    from paper_1402_5670_b300.sharded import filter_ranges
+    rs = filter_ranges(b.R, 2)
+    xh = b.spectrum(x)
+    Cs = [torch.empty((j1 - j0,) + b.dims, device="cuda") for j0, j1 in rs]
+    parts = [torch.empty_like(xh) for _ in rs]
+    y = torch.empty_like(x)
+
+    def run():
+        b.spectrum(x, out=xh)
+        for (j0, j1), C, pt in zip(rs, Cs, parts):
+            b.forward_range(xh, j0, j1, out=C)
+            b.inverse_partial(C, j0, j1, out=pt)
+        parts[0].add_(parts[1])
+        b.inverse_finish(parts[0], True, out=y)
+    ms = _time_graph(run, flush, steps)
+    return {"ranges": rs, "ms": ms, "rel_err_reconstruction": float((y - x).abs().max() / x.abs().max()),
+            "note": "both ranks' work on one GPU, one after the other"}
+
+
 def batched_uneven(flush, steps: int, peak: float) -> dict:
     """64 seeded images with sides drawn from {256, 384, 512, 1024}, four scales,
     levels (1,1,2,2): forward + inverse of the whole batch as one graph launch (after
     the autotuner has picked the group caps and the branch count), against the same
-    images transformed one after another (single-image calls, graph captured)."""
+    images transformed one after another (single-image calls, graph captured). Run in
+    FP32 and with the pencil passes on the tensor cores (BF16 and FP16 operands;
+    images whose first side is 384 stay FP32: the tensor-core stages need a power of
+    two there); the tensor-core modes report their forward error against the FP32
+    batch's coefficients."""
     import torch
     from paper_1402_5670_b300 import synth
     from paper_1402_5670_b300.shearlet import Bank, Batch
     shapes = synth.uneven_batch_shapes(64, (256, 384, 512, 1024), SEED)
-    cache = {}
-    for d in shapes:
-        if d not in cache:
-            cache[d] = Bank(d, J, LEVELS, device=torch.cuda.current_device())
-    banks = [cache[d] for d in shapes]
     xs = [torch.from_numpy(synth.add_noise(synth.piecewise_smooth_image(d, SEED + i), SIGMA,
                                            SEED + 500 + i)).cuda() for i, d in enumerate(shapes)]
-    cs = [torch.empty((b.R,) + b.dims, device="cuda") for b in banks]
-    ys = [torch.empty_like(x) for x in xs]
-    coeffs = sum(b.R * b.N for b in banks)
-    alg = sum(8 * b.N + 8 * b.R * b.N + 8 * b.R * b.Nh + 8 * b.Nh for b in banks)
-    B = Batch(banks)
-    tune_ms = B.autotune(xs, cs, ys, reps=3)
-    info = B.info()
-    st = torch.cuda.current_stream()
-    for _ in range(3):
-        B.fwdinv(xs, cs, ys)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    for a, e in ev:
-        flush.zero_()
-        a.record(st)
-        B.fwdinv(xs, cs, ys)
-        e.record(st)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
-    err = max(float((y - x).abs().max() / x.abs().max()) for x, y in zip(xs, ys))
-
-    def sequential():
-        for b, x, c, y in zip(banks, xs, cs, ys):
-            b.forward(x, out=c)
-            b.inverse(c, out=y)
-
-    ms_seq = _time_graph(sequential, flush, max(3, steps // 3))
-    caps = {f"{d[0]}x{d[1]}": info["group_cap"][shapes.index(d)] for d in cache}
-    res = {"ms": ms, "images": len(shapes), "distinct_shapes": len(cache),
-           "coeffs_per_s": coeffs / (ms * 1e-3), "alg_bytes": alg,
-           "frac_hbm": alg / (ms * 1e-3) / 1e9 / peak, "rel_err_reconstruction": err,
-           "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms,
-           "autotune": {"branches": info["branches"], "group_cap": caps, "best_ms": tune_ms},
-           "launch": "one cudaGraphLaunch per batch (library-captured fork/join graph)"}
-    B.close()
-    del cs
-    for b in cache.values():
-        b.close()
-    return res
+    out = {}
+    ref_cs = None
+    for prec in ("fp32", "tc_bf16", "tc_fp16"):
+        cache = {}
+        for d in shapes:
+            if d not in cache:
+                pr = prec if (prec == "fp32" or d[0] != 384) else "fp32"
+                cache[d] = Bank(d, J, LEVELS, device=torch.cuda.current_device(), precision=pr)
+        banks = [cache[d] for d in shapes]
+        cs = [torch.empty((b.R,) + b.dims, device="cuda") for b in banks]
+        ys = [torch.empty_like(x) for x in xs]
+        coeffs = sum(b.R * b.N for b in banks)
+        alg = sum(8 * b.N + 8 * b.R * b.N + 8 * b.R * b.Nh + 8 * b.Nh for b in banks)
+        B = Batch(banks)
+        tune_ms = B.autotune(xs, cs, ys, reps=3)
+        info = B.info()
+        st = torch.cuda.current_stream()
+        for _ in range(3):
+            B.fwdinv(xs, cs, ys)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, e in ev:
+            flush.zero_()
+            a.record(st)
+            B.fwdinv(xs, cs, ys)
+            e.record(st)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+        err = max(float((y - x).abs().max() / x.abs().max()) for x, y in zip(xs, ys))
+        res = {"ms": ms, "images": len(shapes), "distinct_shapes": len(cache),
+               "coeffs_per_s": coeffs / (ms * 1e-3), "alg_bytes": alg,
+               "frac_hbm": alg / (ms * 1e-3) / 1e9 / peak, "rel_err_reconstruction": err,
+               "autotune": {"branches": info["branches"], "best_ms": tune_ms,
+                            "group_cap": {f"{d[0]}x{d[1]}": info["group_cap"][shapes.index(d)]
+                                          for d in cache}},
+               "launch": "one cudaGraphLaunch per batch (library-captured fork/join graph)"}
+        if prec == "fp32":
+            def sequential():
+                for b, x, c, y in zip(banks, xs, cs, ys):
+                    b.forward(x, out=c)
+                    b.inverse(c, out=y)
+            res["sequential_ms"] = _time_graph(sequential, flush, max(3, steps // 3))
+            res["speedup_vs_sequential"] = res["sequential_ms"] / ms
+            B.forward(xs, cs)
+            torch.cuda.synchronize()
+            ref_cs = [c.clone() for c in cs]
+        else:
+            B.forward(xs, cs)
+            torch.cuda.synchronize()
+            res["max_rel_err_fwd_vs_fp32"] = max(
+                float((c - r).abs().amax(dim=tuple(range(1, c.dim()))).div(
+                    r.abs().amax(dim=tuple(range(1, r.dim())))).max())
+                for c, r in zip(cs, ref_cs))
+            res["fp32_images"] = sum(1 for d in shapes if d[0] == 384)
+        out[prec] = res
+        B.close()
+        del cs
+        for b in cache.values():
+            b.close()
+    del ref_cs
+    return out
 
 
 # ----------------------------------------------------- oracle on the host ---
