@@ -1,7 +1,8 @@
 // Register-resident small DFTs and the two-pass line-FFT decomposition used by every
 // transform kernel of libshearlet. Internal header.
 //
-// A length-L line is split as L = A * B (powers of two, or 384 = 24 * 16). With
+// A length-L line is split as L = A * B (powers of two, 384 = 24 * 16 or 192 = 16 * 12).
+// With
 // n = a + A b and
 // k = kb + B ka,
 //   X[kb + B ka] = sum_a W_A^{a ka} * ( W_L^{a kb} * sum_b x[a + A b] W_B^{b kb} ).
@@ -236,11 +237,14 @@ template <> struct Split<256> { static constexpr int A = 16, B = 16; };
 template <> struct Split<512> { static constexpr int A = 32, B = 16; };
 template <> struct Split<1024> { static constexpr int A = 32, B = 32; };
 template <> struct Split<384> { static constexpr int A = 24, B = 16; };  // 3 * 2^7
+template <> struct Split<192> { static constexpr int A = 16, B = 12; };  // 3 * 2^6 (3D)
 
 // Offset of the twiddle table of length L inside the concatenated table: lengths
-// 8, 16, ..., 1024 back to back (8 + 16 + ... + L/2 = L - 8), then 384.
-__host__ __device__ constexpr int twiddle_offset(int L) { return L == 384 ? 2040 : L - 8; }
-constexpr int kTwiddleTotal = 2040 + 384;
+// 8, 16, ..., 1024 back to back (8 + 16 + ... + L/2 = L - 8), then 384, then 192.
+__host__ __device__ constexpr int twiddle_offset(int L) {
+  return L == 384 ? 2040 : L == 192 ? 2040 + 384 : L - 8;
+}
+constexpr int kTwiddleTotal = 2040 + 384 + 192;
 
 }  // namespace dev
 }  // namespace sl

@@ -45,6 +45,7 @@ __device__ float2 g_twiddle[kTwiddleTotal];
 // several independent CTAs share an SM and overlap each other's memory latency.
 __host__ __device__ constexpr int col_tile_of(int L) {
   return L == 8 ? 32 : L == 16 ? 32 : L == 32 ? 16 : L == 64 ? 16 : L == 128 ? 8 : L == 256 ? 8
+       : L == 192 ? 8
        : 4;  // 384, 512, 1024
 }
 

@@ -252,5 +252,203 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p, int nslots) 
   }
 }
 
+// ------------------------------------------------ planes too large to double-buffer ---
+// Plane pass for L x L planes whose half spectrum [L][L/2 + 1] leaves room for only one
+// plane buffer and a partial exchange in one CTA's shared memory (L = 192: 149 KB plane,
+// 78 KB exchange, 227 KB in total). Persistent, one plane at a time, no prefetch:
+//   * the axis-1 (column) FFT runs on the plane in place, half of the columns at a time
+//     through the exchange;
+//   * the axis-2 row FFTs run on QC row pairs at a time: real rows are read from (R2C)
+//     or written to (C2R) global memory directly, so the plane buffer only ever holds
+//     half spectra (RT keeps each chunk's thresholded rows in the chunk's own part of the
+//     plane buffer until their forward row FFT).
+// Modes as k_plane (ROW_C2R, ROW_R2C, ROW_RT); spectra tile-major (p.tm), real planes
+// row-major.
+constexpr int kBigThreads = 768;
+
+template <int L>
+struct BigPlane {
+  static constexpr int A = Split<L>::A, B = Split<L>::B;
+  static constexpr int NH = L / 2 + 1, H = L / 2;
+  static constexpr int HALF = L * NH;            // plane buffer (half spectrum)
+  static constexpr int LS = B * (A + 1);         // padded row exchange per pair
+  static constexpr int QC = L / 4;               // row pairs per chunk (two chunks)
+  static constexpr int CW = (NH + 1) / 2;        // columns per chunk (two chunks)
+  static constexpr int WROW = QC * LS, WCOL = L * CW;
+  static constexpr int WSZ = WROW > WCOL ? WROW : WCOL;
+  static constexpr int bytes = (HALF + WSZ) * (int)sizeof(float2);
+  static_assert(QC * L <= (L / 2) * NH, "a chunk's natural pairs fit its part of the plane");
+  static_assert(QC * 2 * NH <= WSZ, "a chunk's half rows fit the exchange");
+};
+
+// FFT along axis 1 of columns [c0, c0 + cw) of the half plane P (in place through W).
+// If out is not null the transformed columns go to the tile-major spectrum out (plane
+// i0) instead of back into P. Ends with a CTA barrier.
+template <int L, int DIR>
+__device__ __forceinline__ void big_col_chunk(float2* P, float2* W, int c0, int cw,
+                                              float2* out, const TileMap& tm, int i0) {
+  using G = BigPlane<L>;
+  constexpr int A = G::A, B = G::B, NH = G::NH;
+  const float2* tw = g_twiddle + twiddle_offset(L);
+  for (int it = threadIdx.x; it < cw * A; it += kBigThreads) {
+    const int c = it % cw, a = it / cw;
+    float2 v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = P[(a + A * b) * NH + c0 + c];
+    Dft<B, DIR>::run(v);
+#pragma unroll
+    for (int kb = 1; kb < B; ++kb) v[kb] = ctw<DIR>(v[kb], tw[kb * A + a]);
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) W[(kb * A + a) * cw + c] = v[kb];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < cw * B; it += kBigThreads) {
+    const int c = it % cw, kb = it / cw;
+    float2 w[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) w[a] = W[(kb * A + a) * cw + c];
+    Dft<A, DIR>::run(w);
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) {
+      const int k = kb + B * ka;
+      if (out) out[tm.at(i0, k * NH + c0 + c)] = w[ka];
+      else P[k * NH + c0 + c] = w[ka];
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nslots) {
+  using G = BigPlane<L>;
+  constexpr int A = G::A, B = G::B, NH = G::NH, H = G::H, LS = G::LS, QC = G::QC, CW = G::CW;
+  extern __shared__ float2 sm[];
+  float2* P = sm;             // [L][NH] half spectrum of the plane
+  float2* W = sm + G::HALF;   // exchange
+  const int tid = threadIdx.x;
+  const int L0 = p.n_rows;
+  const int nitems = nslots * L0;
+  const float2* tw = g_twiddle + twiddle_offset(L);
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int slot = item / L0, i0 = item % L0;
+    __syncthreads();  // the previous plane is done with P and W
+    if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
+      const float2* in = p.in_half + (int64_t)slot * p.in_stride;
+      for (int i = tid; i < G::HALF; i += kBigThreads) P[i] = in[p.tm.at(i0, i)];
+      __syncthreads();
+      for (int c0 = 0; c0 < NH; c0 += CW) big_col_chunk<L, 1>(P, W, c0, min(CW, NH - c0), nullptr, p.tm, i0);
+      const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
+      float* outr = nullptr;
+      if constexpr (MODE == ROW_C2R)
+        outr = p.out_real + (int64_t)slot * p.out_stride + (int64_t)i0 * (L * L);
+      for (int q0 = 0; q0 < L / 2; q0 += QC) {
+        // rows (2q, 2q+1), q in [q0, q0 + QC): inverse DFT of the Hermitian-extended pair
+        for (int it = tid; it < QC * A; it += kBigThreads) {
+          const int a = it % A, qq = it / A, q = q0 + qq;
+          const float2* r0 = P + (2 * q) * NH;
+          const float2* r1 = r0 + NH;
+          float2 u[B];
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const int n = a + A * b;
+            float2 ya, yb;
+            if (n <= H) {
+              ya = r0[n];
+              yb = r1[n];
+            } else {
+              ya = cconj(r0[L - n]);
+              yb = cconj(r1[L - n]);
+            }
+            u[b] = make_float2(ya.x - yb.y, ya.y + yb.x);
+          }
+          Dft<B, 1>::run(u);
+#pragma unroll
+          for (int kb = 1; kb < B; ++kb) u[kb] = ctw<1>(u[kb], tw[kb * A + a]);
+#pragma unroll
+          for (int kb = 0; kb < B; ++kb) W[qq * LS + kb * (A + 1) + a] = u[kb];
+        }
+        __syncthreads();  // the chunk's half rows are consumed: its part of P is free
+        float2* nat = P + (2 * q0) * NH;  // RT: the chunk's natural pairs [QC][L]
+        for (int it = tid; it < QC * B; it += kBigThreads) {
+          const int kb = it % B, qq = it / B, q = q0 + qq;
+          float2 w[A];
+#pragma unroll
+          for (int a = 0; a < A; ++a) w[a] = W[qq * LS + kb * (A + 1) + a];
+          Dft<A, 1>::run(w);
+#pragma unroll
+          for (int ka = 0; ka < A; ++ka) {
+            const int k = kb + B * ka;
+            float c0 = w[ka].x * p.scale, c1 = w[ka].y * p.scale;
+            if (p.use_thr) {
+              if (fabsf(c0) < thr) c0 = 0.f;
+              if (fabsf(c1) < thr) c1 = 0.f;
+            }
+            if constexpr (MODE == ROW_C2R) {
+              outr[(2 * q) * L + k] = c0;
+              outr[(2 * q + 1) * L + k] = c1;
+            } else {
+              nat[qq * L + k] = make_float2(c0, c1);
+            }
+          }
+        }
+        __syncthreads();  // W free for the next chunk
+      }
+      if constexpr (MODE == ROW_C2R) continue;
+    }
+
+    // real row pairs (from global for R2C, from each chunk's natural pairs in P for RT)
+    // -> half rows in P -> FFT along axis 1 -> out
+    for (int q0 = 0; q0 < L / 2; q0 += QC) {
+      float2* chunk = P + (2 * q0) * NH;  // the chunk's part of P
+      for (int it = tid; it < QC * A; it += kBigThreads) {
+        const int a = it % A, qq = it / A, q = q0 + qq;
+        float2 v[B];
+        if constexpr (MODE == ROW_R2C) {
+          const float* inr = p.in_real + (int64_t)slot * p.in_stride + (int64_t)i0 * (L * L);
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const int n = a + A * b;
+            v[b] = make_float2(inr[(2 * q) * L + n], inr[(2 * q + 1) * L + n]);
+          }
+        } else {
+#pragma unroll
+          for (int b = 0; b < B; ++b) v[b] = chunk[qq * L + a + A * b];
+        }
+        Dft<B, -1>::run(v);
+#pragma unroll
+        for (int kb = 1; kb < B; ++kb) v[kb] = ctw<-1>(v[kb], tw[kb * A + a]);
+#pragma unroll
+        for (int kb = 0; kb < B; ++kb) W[qq * LS + kb * (A + 1) + a] = v[kb];
+      }
+      __syncthreads();  // the chunk's inputs are consumed
+      // full spectra Z of the chunk's pairs -> the chunk's part of P (natural, [QC][L])
+      for (int it = tid; it < QC * B; it += kBigThreads) {
+        const int kb = it % B, qq = it / B;
+        float2 w[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) w[a] = W[qq * LS + kb * (A + 1) + a];
+        Dft<A, -1>::run(w);
+#pragma unroll
+        for (int ka = 0; ka < A; ++ka) chunk[qq * L + kb + B * ka] = w[ka];
+      }
+      __syncthreads();
+      // split Z = FFT(x0 + i x1) into the two half rows, through W, then into P
+      for (int it = tid; it < QC * NH; it += kBigThreads) {
+        const int qq = it / NH, k = it % NH;
+        const float2 z = chunk[qq * L + k];
+        const float2 w = chunk[qq * L + (k == 0 ? 0 : L - k)];
+        W[(2 * qq) * NH + k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
+        W[(2 * qq + 1) * NH + k] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+      }
+      __syncthreads();
+      for (int i = tid; i < QC * 2 * NH; i += kBigThreads) chunk[i] = W[i];
+      __syncthreads();
+    }
+    float2* out = p.out_half + (int64_t)slot * p.out_stride;
+    for (int c0 = 0; c0 < NH; c0 += CW) big_col_chunk<L, -1>(P, W, c0, min(CW, NH - c0), out, p.tm, i0);
+  }
+}
+
 }  // namespace dev
 }  // namespace sl

@@ -1051,6 +1051,9 @@ sl_status sl_mlp_create(const sl_bank* bank, sl_mlp** out) {
   int ndim = 0, R = 0, J = 0;
   int64_t dims[3];
   if (sl_bank_info(bank, &ndim, dims, &R, &J) != SL_OK) return mfail(SL_EINVAL, "bad bank");
+  for (int i = 0; i < ndim; ++i)  // neighbourhoods are addressed with shifts and masks
+    if (dims[i] & (dims[i] - 1))
+      return mfail(SL_ENOTSUP, "the learned shrinkage needs power-of-two grid sides");
   sl_mlp* M = new sl_mlp();
   M->bank = bank;
   M->ndim = ndim;

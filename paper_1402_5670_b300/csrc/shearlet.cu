@@ -101,10 +101,11 @@ static sl_status init_device(int dev) {
   if (dev < 0 || dev >= 64) return fail(SL_EINVAL, "device ordinal out of range");
   if (g_dev_init[dev]) return SL_OK;
   std::vector<float2> tw(sl::dev::kTwiddleTotal);
-  for (int L : {8, 16, 32, 64, 128, 256, 512, 1024, 384}) {
+  for (int L : {8, 16, 32, 64, 128, 256, 512, 1024, 384, 192}) {
     int A = 0, B = 0;
     switch (L) {
       case 384: A = 24; B = 16; break;
+      case 192: A = 16; B = 12; break;
       case 8: A = 4; B = 2; break;
       case 16: A = 4; B = 4; break;
       case 32: A = 8; B = 4; break;
@@ -167,6 +168,7 @@ static cudaError_t launch_col(int L, dim3 grid, cudaStream_t st, const ColArgs& 
     case 512: return launch_col_t<512, MODE>(grid, st, a);
     case 1024: return launch_col_t<1024, MODE>(grid, st, a);
     case 384: return launch_col_t<384, MODE>(grid, st, a);
+    case 192: return launch_col_t<192, MODE>(grid, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -297,6 +299,7 @@ static cudaError_t launch_col_inv_pipe(int L, int nitems, cudaStream_t st, const
     case 512: return launch_col_inv_pipe_t<512>(nitems, st, a);
     case 1024: return launch_col_inv_pipe_t<1024>(nitems, st, a);
     case 384: return launch_col_inv_pipe_t<384>(nitems, st, a);
+    case 192: return launch_col_inv_pipe_t<192>(nitems, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -312,6 +315,7 @@ static cudaError_t launch_col_fwd_pipe(int L, int nitems, cudaStream_t st, const
     case 512: return launch_col_fwd_pipe_t<512>(nitems, st, a);
     case 1024: return launch_col_fwd_pipe_t<1024>(nitems, st, a);
     case 384: return launch_col_fwd_pipe_t<384>(nitems, st, a);
+    case 192: return launch_col_fwd_pipe_t<192>(nitems, st, a);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -433,8 +437,23 @@ static cudaError_t launch_plane_l2(int L2, dim3 grid, cudaStream_t st, const Row
   }
 }
 
+// 192 x 192 planes: one plane per CTA (no double buffering), one CTA per SM.
+template <int MODE>
+static cudaError_t launch_plane_big(int slots, cudaStream_t st, const RowArgs& a) {
+  auto k = sl::dev::k_plane_big<192, MODE>;
+  constexpr int smem = sl::dev::BigPlane<192>::bytes;
+  cudaError_t e = ensure_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  const int items = slots * a.n_rows;
+  const int grid = std::min(items, persistent_grid(k, sl::dev::kBigThreads, smem, 90000 + MODE));
+  static const char* names[3] = {"plane_r2c", "plane_c2r", "plane_roundtrip"};
+  return timed_launch(names[MODE], st,
+                      [&]() { k<<<grid, sl::dev::kBigThreads, smem, st>>>(a, slots); });
+}
+
 template <int MODE>
 static cudaError_t launch_plane(int L1, int L2, dim3 grid, cudaStream_t st, const RowArgs& a) {
+  if (L1 == 192 && L2 == 192) return launch_plane_big<MODE>((int)grid.y, st, a);
   switch (L1) {
     case 8: return launch_plane_l2<8, MODE>(L2, grid, st, a);
     case 16: return launch_plane_l2<16, MODE>(L2, grid, st, a);
@@ -742,9 +761,11 @@ static sl_status build_filters_impl(int kind, int ndim, const int64_t* dims, int
   spec.full = fullSystem != 0;
   for (int i = 0; i < ndim; ++i) {
     if (dims[i] < 8) return fail(SL_EINVAL, "every dimension must be >= 8");
-    const bool ok = (is_pow2(dims[i]) && dims[i] <= 1024) || (ndim == 2 && dims[i] == 384);
+    const bool ok = (is_pow2(dims[i]) && dims[i] <= 1024) || (ndim == 2 && dims[i] == 384) ||
+                    (ndim == 3 && dims[i] == 192);
     if (!ok)
-      return fail(SL_ENOTSUP, "dimensions must be powers of two in [8, 1024] (2D: or 384)");
+      return fail(SL_ENOTSUP,
+                  "dimensions must be powers of two in [8, 1024] (2D: or 384; 3D: or 192)");
     spec.dims[i] = dims[i];
   }
   for (int j = 0; j < nScales; ++j) {
@@ -753,8 +774,9 @@ static sl_status build_filters_impl(int kind, int ndim, const int64_t* dims, int
     spec.d[j] = shearLevels[j];
   }
   if (ndim == 3) {
-    if (dims[1] > 128 || dims[2] > 128)
-      return fail(SL_ENOTSUP, "3D: axes 1 and 2 must be at most 128 (one plane per CTA)");
+    const bool big = dims[1] == 192 && dims[2] == 192;  // one plane buffer per CTA
+    if (!big && (dims[1] > 128 || dims[2] > 128 || dims[1] == 192 || dims[2] == 192))
+      return fail(SL_ENOTSUP, "3D: axes 1 and 2 must be powers of two up to 128, or both 192");
   }
   if (prec != SL_PREC_FP32) {
     if (path == SL_PATH_CLUSTER)

@@ -54,6 +54,8 @@ def test_status_strings(L):
     ((16, 16, 256), 1, (0,), "SL_ENOTSUP"),    # 3D plane larger than one CTA holds
     ((768, 64), 1, (1,), "SL_ENOTSUP"),        # 3 * 2^8: only 384 has a mixed-radix plan
     ((384, 16, 16), 1, (0,), "SL_ENOTSUP"),    # 384 is a 2D size only
+    ((192, 64), 1, (0,), "SL_ENOTSUP"),        # 192 is a 3D size only
+    ((16, 192, 64), 1, (0,), "SL_ENOTSUP"),    # a 192 plane must be 192 x 192
 ])
 def test_invalid_arguments_are_rejected(L, dims, J, sl, err):
     with pytest.raises(S.ShearletError) as ei:
@@ -73,7 +75,8 @@ CASES = [((64, 64), 3, (0, 1, 1), False), ((64, 32), 2, (1, 1), False),
          ((256, 256), 2, (1, 1), False), ((32, 32), 2, (1, 2), True),
          ((16, 16, 16), 2, (0, 1), False), ((32, 16, 8), 2, (1, 1), False),
          ((16, 16, 16), 1, (1,), True), ((384, 64), 2, (1, 1), False),
-         ((64, 384), 3, (0, 1, 1), False)]
+         ((64, 384), 3, (0, 1, 1), False), ((16, 192, 192), 2, (0, 1), False),
+         ((192, 16, 8), 1, (1,), False)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=str)

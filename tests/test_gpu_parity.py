@@ -60,7 +60,8 @@ CASES_2D = [((16, 16), 1, (1,)), ((32, 32), 2, (0, 1)), ((64, 32), 2, (1, 1)),
             ((32, 128), 2, (1, 2)), ((128, 256), 3, (1, 1, 2)), ((256, 256), 2, (1, 1)),
             ((8, 8), 1, (0,)), ((1024, 64), 2, (1, 1))]
 CASES_3D = [((8, 8, 8), 1, (0,)), ((16, 16, 16), 2, (0, 1)), ((32, 16, 8), 2, (1, 1)),
-            ((16, 32, 64), 2, (1, 1)), ((64, 64, 64), 3, (0, 0, 1))]
+            ((16, 32, 64), 2, (1, 1)), ((64, 64, 64), 3, (0, 0, 1)),
+            ((16, 192, 192), 2, (0, 1)), ((192, 32, 16), 2, (1, 1))]
 CASES = CASES_2D + CASES_3D
 
 
@@ -107,7 +108,8 @@ def test_threshold_bit_exact(case):
     assert np.array_equal(Cg.cpu().numpy(), ref.astype(np.float32))
 
 
-@pytest.mark.parametrize("case", [CASES_2D[2], CASES_2D[5], CASES_3D[1], CASES_3D[2]], ids=str)
+@pytest.mark.parametrize("case", [CASES_2D[2], CASES_2D[5], CASES_3D[1], CASES_3D[2],
+                                  CASES_3D[5]], ids=str)
 def test_denoise_fused_matches_oracle(case):
     dims, J, sl = case
     b = bank(dims, J, sl)
@@ -277,6 +279,27 @@ def test_full_size_3d_128(tmp_path):
     del C
     torch.cuda.empty_cache()
     assert rel(xi, _oracle_inverse_parallel(Cn, dims, J, sl, s, tmp_path)) < TOL
+
+
+def test_full_size_3d_192():
+    """192^3, the paper's video grid (Sec. 5.6), three scales, levels (1,1,2): R = 292.
+    Its 192 x 192 planes take the one-plane-per-CTA kernel and its pencils the 16 x 12
+    split with a radix-3 step. Sampled subbands against the oracle, each against its
+    own size, and perfect reconstruction."""
+    dims, J, sl = (192, 192, 192), 3, (1, 1, 2)
+    b = bank(dims, J, sl)
+    s = oracle_system(dims, J, sl)
+    assert b.R == 292
+    x = signal(dims, 16)
+    C = b.forward(cuda(x))
+    js = (0, 1, 70, 150, 291)
+    ref = O.forward_subset(x.astype(np.float64), s, js)
+    for j in js:
+        assert rel(C[j].cpu().numpy(), ref[j]) < TOL, j
+    xi = b.inverse(C).cpu().numpy()
+    assert rel(xi, x) < TOL
+    del C
+    torch.cuda.empty_cache()
 
 
 def test_full_size_2d_1024():
