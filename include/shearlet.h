@@ -166,19 +166,24 @@ sl_status sl_build_wavelets(int ndim, const int64_t* dims, int nScales, int devi
  * transform of this bank still running on the GPU. */
 void sl_free_filters(sl_bank* bank);
 
-/* Shape of a bank: ndim, dims[0..ndim-1] (host array of 3), R (number of filters),
- * nScales. Any output pointer may be NULL. */
+/* Shape of a bank: ndim, dims[0..ndim-1] (host array of 3), R (number of filters,
+ * the redundancy of Sec. 4.3's table: 1 + sum over scales of the filters per scale of
+ * Secs. 4.1 and 4.4), nScales. Any output pointer may be NULL. */
 sl_status sl_bank_info(const sl_bank* bank, int* ndim, int64_t* dims, int* R,
                        int* nScales);
 
 /* Per-filter metadata (host arrays of R entries; any may be NULL): scale_of[j] in
- * 0..J-1 (-1 for the lowpass), cone_of[j] (2D cone 1/2, 3D pyramid 1..3, 0 for the
- * lowpass), k_of[2j], k_of[2j+1] the shear(s) (2D: k and 0). */
+ * 0..J-1 (-1 for the lowpass), cone_of[j] (2D cone 1/2 of Def. digitSH_alpha and eq.
+ * convolution01, 3D pyramid 1..3 of Def. 3DdigitSH_alpha, 0 for the lowpass),
+ * k_of[2j], k_of[2j+1] the shear parameter(s) k of the digital shear S^d_{k/2^d}
+ * (eqs. dshear1_alpha, dshear2_alpha; 2D: k and 0). */
 sl_status sl_bank_filter_meta(const sl_bank* bank, int* scale_of, int* cone_of,
                               int* k_of);
 
-/* norms[j] = ||psi_j||_2 (host array of R, may be NULL) and the frame bounds
- * A = min Psi, B = max Psi (= 1 after normalisation), FP64. */
+/* norms[j] = ||psi_j||_2 (host array of R, may be NULL; the factor of the threshold of
+ * eq. hard_tresholding) and the frame bounds A = min Psi, B = max Psi of the frame
+ * weight of eq. frame_filter (= 1 after normalisation; the quantities of Sec. 4.3's
+ * table of frame bounds), FP64. */
 sl_status sl_bank_norms(const sl_bank* bank, double* norms, double* A, double* B);
 
 /* The kernel path the bank's transforms take: SL_PATH_GENERAL or SL_PATH_CLUSTER
