@@ -540,18 +540,23 @@ sl_status sl_mlp_train_step(sl_mlp* mlp, const float* noisy, const float* clean,
 /* out[j] = g * coeffs[j] for every subband j >= 1 and out[0] = coeffs[0] (DEVICE
  * [R][dims]; out must not alias coeffs, whose neighbourhoods the features read). */
 sl_status sl_mlp_apply(sl_mlp* mlp, const float* coeffs, float* out, float sigma, void* stream);
-/* Inference engine of sl_mlp_apply: SL_MLP_TCGEN05 (default) runs both layers as
- * tcgen05.mma on tiles of 128 coefficients with the accumulators in tensor memory;
- * SL_MLP_MMA_SYNC runs them as warp-level mma.sync on tiles of 16 (the kernel the
- * training step shares). Same BF16 operands and FP32 accumulation; sums may round in
- * another order. SL_EINVAL for another value. */
+/* Engine of sl_mlp_apply, sl_mlp_gradients and sl_mlp_train_step. SL_MLP_TCGEN05
+ * (default): tcgen05.mma on tiles of 128 samples with the accumulators in tensor
+ * memory; training runs the forward and backward products and the weight-gradient
+ * sums over each CTA's tiles there, and adds the CTAs' partial gradients in a fixed
+ * order (SL_ENOTSUP from training when R * 32 bytes of embedding gradients do not fit
+ * the CTA's shared memory beside its tiles, R above about 2900). SL_MLP_MMA_SYNC:
+ * warp-level mma.sync on tiles of 16, gradients summed with atomics. Same BF16 operands
+ * and FP32 accumulation; sums may round in another order. SL_EINVAL for another
+ * value. */
 #define SL_MLP_TCGEN05 0
 #define SL_MLP_MMA_SYNC 1
 sl_status sl_mlp_set_engine(sl_mlp* mlp, int engine);
 /* Synchronises the stream and reports whether a tensor-core wait of an earlier
- * sl_mlp_apply ran out (each wait gives up after about two seconds, sets a device flag
- * and the kernel returns with that tile's output unwritten): SL_ECUDA and the flag
- * cleared if so, SL_OK otherwise. */
+ * sl_mlp_apply or training call ran out (each wait gives up after about two seconds,
+ * sets a device flag and the kernel returns: apply with that tile's output unwritten,
+ * training with that CTA's gradient share dropped): SL_ECUDA and the flag cleared if
+ * so, SL_OK otherwise. */
 sl_status sl_mlp_check(sl_mlp* mlp, void* stream);
 /* Learned denoising: sl_forward, sl_mlp_apply, sl_inverse (DEVICE [dims] arrays; the
  * first call allocates 2 R N floats of coefficient memory kept by the MLP). */

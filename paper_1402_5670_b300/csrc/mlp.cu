@@ -304,15 +304,18 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
-// N = 64, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
-                            ((128u >> 4) << 24);
+// M = 128 and N (a multiple of 16, 16..256).
+__host__ __device__ constexpr uint32_t idesc_m128(uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+constexpr uint32_t kIdesc = idesc_m128(64);
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc,
+                                          uint32_t idesc = kIdesc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -356,6 +359,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tc_before_sync() {
@@ -408,18 +426,17 @@ struct TcApplySmem {
 // FP32 master parameters -> the BF16 K-major weight tiles of TcWeights, one element
 // per thread over w1, w2, w3 and b3 in turn.
 template <int NDIM>
-constexpr int tc_pack_elems() { return H * Net<NDIM>::KP + H * K2 + H + 4; }
+__host__ __device__ constexpr int tc_pack_elems() { return H * Net<NDIM>::KP + H * K2 + H + 4; }
 
 template <int NDIM>
-__global__ void __launch_bounds__(256) k_mlp_pack_tc(const float* __restrict__ prm,
-                                                     TcWeights<NDIM>* __restrict__ out) {
+__device__ __forceinline__ void pack_tc_one(const float* __restrict__ prm,
+                                            TcWeights<NDIM>* __restrict__ out, int i) {
   using NN = Net<NDIM>;
   constexpr int F = NN::F, KP = NN::KP;
   auto split = [](float b, bool lo_part) {
     const __nv_bfloat16 hi = __float2bfloat16_rn(b);
     return lo_part ? __float2bfloat16_rn(b - __bfloat162float(hi)) : hi;
   };
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < H * KP) {
     const int o = i / KP, k = i % KP;
     __nv_bfloat16 w = __float2bfloat16_rn(0.f);
@@ -444,6 +461,12 @@ __global__ void __launch_bounds__(256) k_mlp_pack_tc(const float* __restrict__ p
   }
   i -= H;
   if (i < 4) out->b3[i] = i == 0 ? prm[NN::ob3] : 0.f;
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) k_mlp_pack_tc(const float* __restrict__ prm,
+                                                     TcWeights<NDIM>* __restrict__ out) {
+  pack_tc_one<NDIM>(prm, out, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Read-only global load that the compiler keeps where it is written (a prefetch a
@@ -692,6 +715,480 @@ static int apply_tc_grid() {
     grid[dev] = std::max(1, per_sm) * sm_count();
   }
   return grid[dev];
+}
+
+// ---------------------------------------------- training on tcgen05 tensor cores ---
+// One CTA of 4 warps per SM walks tiles of 128 samples (thread t owns row t, TMEM lane
+// t). Per tile, one thread issues five products, each accumulating in tensor memory:
+//   z1  = [x, 1, 1] [W1, b1]^T            (128 x 64, K = KP)     -> columns 0..63
+//   z2  = [h1, 1, 1] [W2, b2]^T           (128 x 64, K = K2)     -> columns 0..63
+//   dh1 = dz2 W2                          (128 x 64, K = 64)     -> columns 0..63
+//   D1 += [dz2 ; dz1]^T [x ; h1]          (128 x (KP + 64), K = 128 rows of the tile)
+//   D2 += [h2 ; x ; h1]^T [dz3, 0 ..]     (128 x 16, K = 128)
+// The last two carry the weight gradients across the CTA's tiles: D1 holds dW2 (dz2
+// rows x h1 columns), dW1 (dz1 rows x feature columns), and through the constant-one
+// feature columns b2's and b1's gradients; D2 holds w3's gradient (h2 rows) and b3's
+// (the one-row of x). The cross blocks (dz2 x features, dz1 x h1, ...) are computed
+// and ignored: they keep both products at M = 128. The gradient of the subband
+// embedding (dx for the embedding features, a 64 x 8 product per row) is summed on the
+// CUDA cores into a per-CTA table in shared memory. At the end every CTA writes its
+// gradients and its loss as one row of a partial-sum table; k_mlp_reduce adds the rows
+// in a fixed order (and applies Adam).
+// The weight-gradient operands are K-major over the tile's rows (element (m, r) of a
+// [M][128] tile), written with one 2-byte store per value; their core matrices sit
+// 144 bytes apart along K (128 + 16 of padding) so that the four 8-lane groups of a
+// warp store into different banks.
+constexpr int TT_THREADS = 128;
+constexpr int TT_TMEM_COLS = 256;
+constexpr int KR = 128;                  // rows per tile = K of the weight-gradient products
+constexpr int KR_LBO = 144;              // K-direction core-matrix stride of those operands
+constexpr int KR_SBO = (KR / 8) * KR_LBO;  // 8-row block stride
+
+__host__ __device__ __forceinline__ int kmajor_r(int m, int r) {
+  return (m >> 3) * KR_SBO + (r >> 3) * KR_LBO + (m & 7) * 16 + (r & 7) * 2;
+}
+
+// Weights of one training CTA: the inference tiles plus W2 transposed (the B operand of
+// dz2 W2: element (i, o) = W2[o][i], K-major over o) and W1's embedding columns
+// rounded to BF16 (as FP32 values, [o][e]).
+template <int NDIM>
+struct TcTrainWeights {
+  TcWeights<NDIM> base;
+  alignas(16) unsigned char w2t[H * H * 2];
+  alignas(16) float w1e[H * EMB];
+};
+
+template <int NDIM>
+__host__ __device__ constexpr int tc_train_pack_elems() { return tc_pack_elems<NDIM>() + H * H + H * EMB; }
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) k_mlp_pack_train(const float* __restrict__ prm,
+                                                        TcTrainWeights<NDIM>* __restrict__ out) {
+  using NN = Net<NDIM>;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < tc_pack_elems<NDIM>()) {
+    pack_tc_one<NDIM>(prm, &out->base, i);
+    return;
+  }
+  i -= tc_pack_elems<NDIM>();
+  if (i < H * H) {
+    const int n = i / H, o = i % H;  // W2^T row n = hidden unit i of h1, K index o
+    *reinterpret_cast<__nv_bfloat16*>(out->w2t + kmajor(n, o, H)) =
+        __float2bfloat16_rn(prm[NN::oW2 + o * H + n]);
+    return;
+  }
+  i -= H * H;
+  if (i < H * EMB) {
+    const int o = i / EMB, e = i % EMB;
+    out->w1e[i] = __bfloat162float(__float2bfloat16_rn(prm[NN::oW1 + o * NN::F + 1 + NN::NB + e]));
+  }
+}
+
+template <int NDIM>
+struct TcTrainSmem {
+  static constexpr int KP = Net<NDIM>::KP;
+  static constexpr int TR = 128 + KP;  // rows of tt
+  TcTrainWeights<NDIM> w;
+  // features [128][KP], then [h1, 1, 1, 0..] [128][K2], then dz2 [128][64] (K-major)
+  alignas(16) unsigned char act[TC_ROWS * K2 * 2];
+  alignas(16) unsigned char aw1[(128 / 8) * KR_SBO];  // [dz2^T ; dz1^T]      [128][KR]
+  alignas(16) unsigned char tt[(TR / 8) * KR_SBO];    // [h2^T ; x^T ; h1^T]  [TR][KR]
+  alignas(16) unsigned char bw2[(16 / 8) * KR_SBO];   // [dz3 ; 0 x 15]       [16][KR]
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
+  float red[TT_THREADS / 32];
+  // followed by the CTA's embedding-gradient table, R x EMB floats
+};
+
+template <int NDIM>
+constexpr size_t tc_train_smem_bytes(int R) {
+  return sizeof(TcTrainSmem<NDIM>) + (size_t)R * EMB * sizeof(float);
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char* base, int off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(TT_THREADS, 1)
+    k_mlp_train_tc(MlpArgs a, const TcTrainWeights<NDIM>* __restrict__ wg, float* __restrict__ parts,
+                   int stride, int* err, long long wait_limit) {
+  using NN = Net<NDIM>;
+  using SM = TcTrainSmem<NDIM>;
+  constexpr int F = NN::F, KP = NN::KP, NB = NN::NB;
+  constexpr int CENTRE = NB / 2;
+  constexpr int NW1 = KP + H;                 // columns of D1: features, then h1
+  constexpr int C_D1 = H, C_D2 = H + NW1;     // tensor-memory columns of D1 and D2
+  static_assert(C_D2 + 16 <= TT_TMEM_COLS, "tensor-memory budget");
+  static_assert(NW1 % 16 == 0 && NW1 <= 256, "N of the D1 product");
+  static_assert(64 + F < 128, "the one-row of x lies inside D2's 128 rows");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SM& S = *reinterpret_cast<SM*>(smraw);
+  float* sE = reinterpret_cast<float*>(smraw + sizeof(SM));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&S.tmem)),
+                 "n"(TT_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  {
+    constexpr int n16 = (int)(sizeof(TcTrainWeights<NDIM>) / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(wg);
+    uint4* dst = reinterpret_cast<uint4*>(&S.w);
+    for (int i = tid; i < n16; i += TT_THREADS) dst[i] = __ldg(src + i);
+  }
+  for (int i = tid; i < a.R * EMB; i += TT_THREADS) sE[i] = 0.f;
+  // rows that never change: x^T's two bias ones and its zero padding, bw2's zero rows
+#pragma unroll
+  for (int k = F; k < KP; ++k) st_bf16(S.tt, kmajor_r(64 + k, tid), k < F + 2 ? 1.f : 0.f);
+#pragma unroll
+  for (int m = 1; m < 16; ++m) st_bf16(S.bw2, kmajor_r(m, tid), 0.f);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const float* E = a.prm + NN::oE;
+  const int lgN = a.geo.lg[0] + a.geo.lg[1] + a.geo.lg[2];
+  const int tiles = a.n / TC_ROWS;
+  const float inv_n = 1.f / (float)a.n;
+  const uint32_t act = smem_addr(S.act), w1 = smem_addr(S.w.base.w1), w2 = smem_addr(S.w.base.w2),
+                 w2t = smem_addr(S.w.w2t), aw1 = smem_addr(S.aw1), tt = smem_addr(S.tt),
+                 bw2 = smem_addr(S.bw2);
+  constexpr uint32_t kOnes = 0x3F803F80u;  // two BF16 ones
+  // sample indices are clamped to subbands 1..R-1 so that a bad index cannot read
+  // outside the stacks (the API requires valid indices)
+  const int64_t qlo = a.geo.N, qhi = (int64_t)a.R * a.geo.N - 1;
+  float nb[NB];
+  float cc_next = 0.f;
+  int64_t q_next = qlo;
+  auto gather = [&](int t) {  // this thread's sample of tile t, loaded a tile ahead
+    if (t < tiles) {
+      const int64_t q = min(max((int64_t)__ldg(a.idx + (int64_t)t * TC_ROWS + tid), qlo), qhi);
+      q_next = q;
+      gather_nb<NDIM>(a.geo, a.C + ((q >> lgN) << lgN), (uint32_t)(q & (a.geo.N - 1)), nb);
+      cc_next = ld_early(a.Cc + q);
+    }
+  };
+  gather(blockIdx.x);
+  // The mbarrier completes four phases per tile: layer 1 (parity 0), layer 2 (1), dh1
+  // (0), the weight-gradient products (1, waited for at the next tile's start). A wait
+  // that runs out is made CTA-uniform at the next barrier and ends the loop there.
+  float loss_acc = 0.f;
+  int timed_out = 0;     // CTA-uniform
+  uint32_t pending = 0;  // parity of the phase a timed-out wait left in flight
+  bool late = false;     // this warp's last wait ran out (warp-uniform)
+  bool first = true;     // no weight-gradient product issued yet (CTA-uniform)
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    // the previous tile's weight-gradient products read aw1, tt and bw2
+    if (!first) late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
+    tc_after_sync();
+    const int64_t q = q_next;
+    const int j = (int)(q >> lgN);
+    const float c = nb[CENTRE], cc = cc_next;
+    const float is = a.inv_s[j];
+    if (!late) {
+      float x[KP];
+      x[0] = c * is;
+#pragma unroll
+      for (int d = 0; d < NB; ++d) x[1 + d] = fabsf(nb[d]) * is;
+#pragma unroll
+      for (int e = 0; e < EMB; ++e) x[1 + NB + e] = __ldg(E + j * EMB + e);
+      x[F] = 1.f;
+      x[F + 1] = 1.f;
+#pragma unroll
+      for (int k = F + 2; k < KP; ++k) x[k] = 0.f;
+#pragma unroll
+      for (int k8 = 0; k8 < KP / 8; ++k8)
+        *reinterpret_cast<uint4*>(S.act + kmajor(tid, 8 * k8, KP)) =
+            make_uint4(pack_bf16(x[8 * k8], x[8 * k8 + 1]), pack_bf16(x[8 * k8 + 2], x[8 * k8 + 3]),
+                       pack_bf16(x[8 * k8 + 4], x[8 * k8 + 5]),
+                       pack_bf16(x[8 * k8 + 6], x[8 * k8 + 7]));
+#pragma unroll
+      for (int k = 0; k < F; ++k) st_bf16(S.tt, kmajor_r(64 + k, tid), x[k]);
+    }
+    fence_async_smem();
+    tc_before_sync();
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 1;
+      break;
+    }
+    tc_after_sync();
+    // z1 = [x, 1, 1] [W1, b1]^T
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KP / 16; ++ks)
+        umma_bf16(tmem, umma_desc(act + ks * 256, 128, (KP / 8) * 128),
+                  umma_desc(w1 + ks * 256, 128, (KP / 8) * 128), ks > 0);
+      umma_commit(&S.bar);
+    }
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0, wait_limit));
+    tc_after_sync();
+    uint32_t mask[2] = {0u, 0u};  // z1 > 0
+    if (!late) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float z[32];
+        tmem_ld32(tmem + lane_base + 32 * h, z);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) mask[h] |= (z[i] > 0.f ? 1u : 0u) << i;
+#pragma unroll
+        for (int k8 = 0; k8 < 4; ++k8)
+          *reinterpret_cast<uint4*>(S.act + kmajor(tid, 32 * h + 8 * k8, K2)) =
+              make_uint4(relu_pack_bf16(z[8 * k8], z[8 * k8 + 1]),
+                         relu_pack_bf16(z[8 * k8 + 2], z[8 * k8 + 3]),
+                         relu_pack_bf16(z[8 * k8 + 4], z[8 * k8 + 5]),
+                         relu_pack_bf16(z[8 * k8 + 6], z[8 * k8 + 7]));
+#pragma unroll
+        for (int i = 0; i < 32; ++i) st_bf16(S.tt, kmajor_r(64 + KP + 32 * h + i, tid), fmaxf(z[i], 0.f));
+      }
+      *reinterpret_cast<uint4*>(S.act + kmajor(tid, H, K2)) = make_uint4(kOnes, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(S.act + kmajor(tid, H + 8, K2)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    fence_async_smem();
+    tc_before_sync();
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 0;
+      break;
+    }
+    tc_after_sync();
+    gather(t + gridDim.x);  // the next tile's loads overlap the rest of this one
+    // z2 = [h1, 1, 1] [W2, b2]^T
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < K2 / 16; ++ks)
+        umma_bf16(tmem, umma_desc(act + ks * 256, 128, (K2 / 8) * 128),
+                  umma_desc(w2 + ks * 256, 128, (K2 / 8) * 128), ks > 0);
+      umma_commit(&S.bar);
+    }
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
+    tc_after_sync();
+    if (!late) {
+      float za[32], zb[32];
+      tmem_ld32(tmem + lane_base, za);
+      tmem_ld32(tmem + lane_base + 32, zb);
+      const float* w3 = S.w.base.w3;
+      float acc[4] = {S.w.base.b3[0], 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        acc[0] += fmaxf(za[i], 0.f) * w3[i] + fmaxf(zb[i], 0.f) * w3[32 + i];
+        acc[1] += fmaxf(za[i + 1], 0.f) * w3[i + 1] + fmaxf(zb[i + 1], 0.f) * w3[33 + i];
+        acc[2] += fmaxf(za[i + 2], 0.f) * w3[i + 2] + fmaxf(zb[i + 2], 0.f) * w3[34 + i];
+        acc[3] += fmaxf(za[i + 3], 0.f) * w3[i + 3] + fmaxf(zb[i + 3], 0.f) * w3[35 + i];
+      }
+      const float g = 1.f / (1.f + expf(-((acc[0] + acc[1]) + (acc[2] + acc[3]))));
+      const float res = (g * c - cc) * is;
+      loss_acc += res * res;
+      const float dz3 = 2.f * res * c * is * inv_n * g * (1.f - g);
+      float dz2[H];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        dz2[i] = za[i] > 0.f ? dz3 * w3[i] : 0.f;
+        dz2[32 + i] = zb[i] > 0.f ? dz3 * w3[32 + i] : 0.f;
+      }
+      // dz2 as the A operand of dh1 (act is free: layer 2 is done) and as rows of aw1;
+      // h2 as rows of tt; dz3 as the one live row of bw2
+#pragma unroll
+      for (int k8 = 0; k8 < H / 8; ++k8)
+        *reinterpret_cast<uint4*>(S.act + kmajor(tid, 8 * k8, H)) =
+            make_uint4(pack_bf16(dz2[8 * k8], dz2[8 * k8 + 1]),
+                       pack_bf16(dz2[8 * k8 + 2], dz2[8 * k8 + 3]),
+                       pack_bf16(dz2[8 * k8 + 4], dz2[8 * k8 + 5]),
+                       pack_bf16(dz2[8 * k8 + 6], dz2[8 * k8 + 7]));
+#pragma unroll
+      for (int i = 0; i < H; ++i) st_bf16(S.aw1, kmajor_r(i, tid), dz2[i]);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        st_bf16(S.tt, kmajor_r(i, tid), fmaxf(za[i], 0.f));
+        st_bf16(S.tt, kmajor_r(32 + i, tid), fmaxf(zb[i], 0.f));
+      }
+      st_bf16(S.bw2, kmajor_r(0, tid), dz3);
+    }
+    fence_async_smem();
+    tc_before_sync();
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 1;
+      break;
+    }
+    tc_after_sync();
+    // dh1 = dz2 W2
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < H / 16; ++ks)
+        umma_bf16(tmem, umma_desc(act + ks * 256, 128, (H / 8) * 128),
+                  umma_desc(w2t + ks * 256, 128, (H / 8) * 128), ks > 0);
+      umma_commit(&S.bar);
+    }
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0, wait_limit));
+    tc_after_sync();
+    if (!late) {
+      // dz1 = dh1 [z1 > 0], rounded to BF16 as the products see it; rows of aw1; and
+      // the embedding gradient dz1 W1[:, embedding] into the CTA's table
+      float ge[EMB];
+#pragma unroll
+      for (int e = 0; e < EMB; ++e) ge[e] = 0.f;
+      const float4* w1e = reinterpret_cast<const float4*>(S.w.w1e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float d[32];
+        tmem_ld32(tmem + lane_base + 32 * h, d);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int o = 32 * h + i;
+          const __nv_bfloat16 vb = __float2bfloat16_rn((mask[h] >> i) & 1u ? d[i] : 0.f);
+          *reinterpret_cast<__nv_bfloat16*>(S.aw1 + kmajor_r(64 + o, tid)) = vb;
+          const float v = __bfloat162float(vb);
+          const float4 wa = w1e[2 * o], wb = w1e[2 * o + 1];
+          ge[0] += v * wa.x;
+          ge[1] += v * wa.y;
+          ge[2] += v * wa.z;
+          ge[3] += v * wa.w;
+          ge[4] += v * wb.x;
+          ge[5] += v * wb.y;
+          ge[6] += v * wb.z;
+          ge[7] += v * wb.w;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < EMB; ++e) atomicAdd(sE + j * EMB + e, ge[e]);
+    }
+    fence_async_smem();
+    tc_before_sync();
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 0;
+      break;
+    }
+    tc_after_sync();
+    // D1 += [dz2 ; dz1]^T [x ; h1],  D2 += [h2 ; x ; h1]^T [dz3, 0 ..]
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ++ks)
+        umma_bf16(tmem + C_D1, umma_desc(aw1 + ks * 2 * KR_LBO, KR_LBO, KR_SBO),
+                  umma_desc(tt + 8 * KR_SBO + ks * 2 * KR_LBO, KR_LBO, KR_SBO),
+                  (!first || ks > 0) ? 1u : 0u, idesc_m128(NW1));
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ++ks)
+        umma_bf16(tmem + C_D2, umma_desc(tt + ks * 2 * KR_LBO, KR_LBO, KR_SBO),
+                  umma_desc(bw2 + ks * 2 * KR_LBO, KR_LBO, KR_SBO),
+                  (!first || ks > 0) ? 1u : 0u, idesc_m128(16));
+      umma_commit(&S.bar);
+    }
+    first = false;
+  }
+  if (!timed_out && !first) {
+    late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
+    tc_after_sync();
+    if (__syncthreads_or(late)) {
+      timed_out = 1;
+      pending = 1;
+    }
+  }
+  if (timed_out) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // let the products in flight finish (bounded by the default limit) before the
+      // tensor memory is freed
+      mbar_wait(&S.bar, pending);
+    }
+    // this CTA's share is dropped (a zero row): the call reports the timeout
+    float* row = parts + (size_t)blockIdx.x * stride;
+    for (int i = tid; i <= NN::oE + a.R * EMB; i += TT_THREADS) row[i] = 0.f;
+    __syncthreads();
+  } else {
+    // this CTA's row of the partial-sum table: every gradient entry and the loss
+    float* row = parts + (size_t)blockIdx.x * stride;
+    const int m = tid;  // TMEM lane = row of D1 and D2
+    if (first) {        // no tile: zero gradients
+      for (int i = tid; i < NN::oE; i += TT_THREADS) row[i] = 0.f;
+    } else {
+#pragma unroll
+      for (int c0 = 0; c0 < NW1; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + C_D1 + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = c0 + i;
+          if (m < H) {  // dz2 rows: b2 through the first one-column, W2 through h1
+            if (n == F) row[NN::ob2 + m] = v[i];
+            else if (n >= KP) row[NN::oW2 + m * H + (n - KP)] = v[i];
+          } else {      // dz1 rows: W1 through the features, b1 through the one-column
+            const int o = m - H;
+            if (n < F) row[NN::oW1 + o * F + n] = v[i];
+            else if (n == F) row[NN::ob1 + o] = v[i];
+          }
+        }
+      }
+      float v[16];
+      tmem_ld16(tmem + lane_base + C_D2, v);
+      if (m < H) row[NN::ow3 + m] = v[0];
+      if (m == H + F) row[NN::ob3] = v[0];
+    }
+    float l = loss_acc;
+#pragma unroll
+    for (int sft = 16; sft > 0; sft >>= 1) l += __shfl_xor_sync(0xffffffffu, l, sft);
+    if (lane == 0) S.red[warp] = l;
+    __syncthreads();  // also orders the embedding table's atomics before its copy
+    const int P = NN::oE + a.R * EMB;
+    if (tid == 0) {
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < TT_THREADS / 32; ++w) s += S.red[w];
+      row[P] = s * inv_n;
+    }
+    for (int i = tid; i < a.R * EMB; i += TT_THREADS) row[NN::oE + i] = sE[i];
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "n"(TT_TMEM_COLS));
+}
+
+// Sum of the training CTAs' partial rows, in row order (the same sum on every run for
+// the same rows): grad[i] for i < P and the loss from column P; with adam != 0 also
+// the Adam update of parameter i (as k_adam). A CTA covers 32 columns, its 8 warps
+// stride over the rows.
+__global__ void __launch_bounds__(256) k_mlp_reduce(const float* __restrict__ parts, int nparts,
+                                                    int stride, int P, float* __restrict__ grad,
+                                                    float* __restrict__ loss, float* __restrict__ p,
+                                                    float* __restrict__ m, float* __restrict__ v,
+                                                    float lr, float c1, float c2, int adam) {
+  __shared__ float sh[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (i <= P)
+    for (int r = w; r < nparts; r += 8) s += parts[(size_t)r * stride + i];
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || i > P) return;
+  float t = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += sh[k][lane];
+  if (i == P) {
+    *loss = t;
+    return;
+  }
+  grad[i] = t;
+  if (adam) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float mi = b1 * m[i] + (1.f - b1) * t;
+    const float vi = b2 * v[i] + (1.f - b2) * t * t;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
 }
 
 // Training: forward and backward on a sample; gradients accumulate into a.grad.
@@ -1006,6 +1503,9 @@ struct sl_mlp {
   bool tc_packed = false;  // tc_pack holds the current parameters (packed on pack_stream)
   cudaStream_t pack_stream = nullptr;
   int engine = SL_MLP_TCGEN05;
+  float* parts = nullptr;  // tensor-core training: one partial-sum row per CTA
+  int pstride = 0;         // floats per partial row (P gradients, the loss, padding)
+  int nparts_max = 0;      // rows (one training CTA per SM)
   float* coeffs = nullptr; // [2][R][N] for sl_mlp_denoise (allocated on first use)
   std::vector<double> norms;
   int t = 0;
@@ -1038,6 +1538,92 @@ static sl_status set_sigma(sl_mlp* M, float sigma, cudaStream_t st) {
       cudaSuccess)
     return mfail(SL_ECUDA, "uploading 1/s");
   M->sigma_set = sigma;
+  return SL_OK;
+}
+
+// Per-wait limit in SM cycles of the tensor-core kernels: the default (about two
+// seconds), or the value of SL_MLP_WAIT_CYCLES, a test hook that makes the waits run
+// out on purpose so that the timeout path (flag, drain, free, sl_mlp_check) can be
+// exercised.
+static long long tc_wait_limit() {
+  long long limit = kTcWaitCycles;
+  if (const char* e = std::getenv("SL_MLP_WAIT_CYCLES")) limit = std::max(0LL, std::atoll(e));
+  return limit;
+}
+
+template <int NDIM>
+static sl_status train_tc(sl_mlp* M, const MlpArgs& a, int tiles, cudaStream_t st, int* grid) {
+  const size_t sm = tc_train_smem_bytes<NDIM>(M->R);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (sm > (size_t)optin)
+    return mfail(SL_ENOTSUP, "too many subbands for the tensor-core trainer's shared memory "
+                             "(select SL_MLP_MMA_SYNC)");
+  cudaFuncSetAttribute(k_mlp_train_tc<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto* wt = reinterpret_cast<TcTrainWeights<NDIM>*>(M->tc_pack);
+  k_mlp_pack_train<NDIM><<<(tc_train_pack_elems<NDIM>() + 255) / 256, 256, 0, st>>>(M->prm, wt);
+  M->tc_packed = false;  // the packed inference tiles are overwritten
+  *grid = std::min(tiles, M->nparts_max);
+  k_mlp_train_tc<NDIM><<<*grid, TT_THREADS, sm, st>>>(a, wt, M->parts, M->pstride, M->tc_err,
+                                                      tc_wait_limit());
+  return SL_OK;
+}
+
+// Gradients (and the loss) of one sample into M->grad / M->loss; with adam, also one
+// Adam step of the parameters (M->t counts the steps).
+static sl_status train_launch(sl_mlp* M, const float* noisy, const float* clean, float sigma,
+                              const int* idx, int n, cudaStream_t st, bool adam, float lr) {
+  if (!M || !noisy || !clean || !idx) return mfail(SL_EINVAL, "NULL argument");
+  if (n <= 0 || n % ROWS) return mfail(SL_EINVAL, "n must be a positive multiple of 128");
+  sl_status s = set_sigma(M, sigma, st);
+  if (s != SL_OK) return s;
+  MlpArgs a{};
+  a.prm = M->prm;
+  a.C = noisy;
+  a.Cc = clean;
+  a.idx = idx;
+  a.n = n;
+  a.inv_s = M->inv_s;
+  a.grad = M->grad;
+  a.loss = M->loss;
+  a.geo = M->geo;
+  a.R = M->R;
+  const int tiles = n / ROWS;
+  float c1 = 1.f, c2 = 1.f;
+  if (adam) {
+    M->t += 1;
+    c1 = 1.f - std::pow(0.9f, (float)M->t);
+    c2 = 1.f - std::pow(0.999f, (float)M->t);
+  }
+  if (M->engine == SL_MLP_TCGEN05) {
+    int grid = 0;
+    s = M->ndim == 2 ? train_tc<2>(M, a, tiles, st, &grid) : train_tc<3>(M, a, tiles, st, &grid);
+    if (s != SL_OK) return s;
+    k_mlp_reduce<<<(M->P + 1 + 31) / 32, 256, 0, st>>>(M->parts, grid, M->pstride, M->P, M->grad,
+                                                      M->loss, M->prm, M->m, M->v, lr, c1, c2,
+                                                      adam ? 1 : 0);
+  } else {
+    if (cudaMemsetAsync(M->grad, 0, M->P * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(M->loss, 0, sizeof(float), st) != cudaSuccess)
+      return mfail(SL_ECUDA, "memset");
+    const int grid = std::min(tiles, 4 * sm_count());
+    if (M->ndim == 2) {
+      const size_t sm = train_smem<2>();
+      cudaFuncSetAttribute(k_mlp_train<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_mlp_train<2><<<grid, 32 * WARPS, sm, st>>>(a);
+    } else {
+      const size_t sm = train_smem<3>();
+      cudaFuncSetAttribute(k_mlp_train<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_mlp_train<3><<<grid, 32 * WARPS, sm, st>>>(a);
+    }
+    if (adam) {
+      M->tc_packed = false;
+      k_adam<<<(M->P + 255) / 256, 256, 0, st>>>(M->prm, M->grad, M->m, M->v, M->P, lr, c1, c2);
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("training step: ") + cudaGetErrorString(e));
   return SL_OK;
 }
 
@@ -1075,8 +1661,12 @@ sl_status sl_mlp_create(const sl_bank* bank, sl_mlp** out) {
             cudaMalloc(&M->loss, sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->inv_s, R * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&M->tc_err, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&M->tc_pack, std::max(sizeof(TcWeights<2>), sizeof(TcWeights<3>))) ==
-                cudaSuccess;
+            cudaMalloc(&M->tc_pack, std::max(sizeof(TcTrainWeights<2>),
+                                             sizeof(TcTrainWeights<3>))) == cudaSuccess;
+  M->pstride = (M->P + 1 + 3) / 4 * 4;
+  M->nparts_max = sm_count();
+  if (ok)
+    ok = cudaMalloc(&M->parts, (size_t)M->nparts_max * M->pstride * sizeof(float)) == cudaSuccess;
   if (ok) ok = cudaMemset(M->prm, 0, M->P * sizeof(float)) == cudaSuccess &&
                cudaMemset(M->tc_err, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(M->m, 0, M->P * sizeof(float)) == cudaSuccess &&
@@ -1100,6 +1690,7 @@ void sl_mlp_free(sl_mlp* M) {
   cudaFree(M->inv_s);
   cudaFree(M->tc_err);
   cudaFree(M->tc_pack);
+  cudaFree(M->parts);
   cudaFree(M->coeffs);
   delete M;
 }
@@ -1173,47 +1764,11 @@ sl_status sl_mlp_load(sl_mlp* M, const char* path) {
   return SL_OK;
 }
 
-static sl_status train_launch(sl_mlp* M, const float* noisy, const float* clean, float sigma,
-                              const int* idx, int n, cudaStream_t st) {
-  if (!M || !noisy || !clean || !idx) return mfail(SL_EINVAL, "NULL argument");
-  if (n <= 0 || n % ROWS) return mfail(SL_EINVAL, "n must be a positive multiple of 128");
-  sl_status s = set_sigma(M, sigma, st);
-  if (s != SL_OK) return s;
-  if (cudaMemsetAsync(M->grad, 0, M->P * sizeof(float), st) != cudaSuccess ||
-      cudaMemsetAsync(M->loss, 0, sizeof(float), st) != cudaSuccess)
-    return mfail(SL_ECUDA, "memset");
-  MlpArgs a{};
-  a.prm = M->prm;
-  a.C = noisy;
-  a.Cc = clean;
-  a.idx = idx;
-  a.n = n;
-  a.inv_s = M->inv_s;
-  a.grad = M->grad;
-  a.loss = M->loss;
-  a.geo = M->geo;
-  a.R = M->R;
-  const int tiles = n / ROWS;
-  const int grid = std::min(tiles, 4 * sm_count());
-  if (M->ndim == 2) {
-    const size_t sm = train_smem<2>();
-    cudaFuncSetAttribute(k_mlp_train<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_mlp_train<2><<<grid, 32 * WARPS, sm, st>>>(a);
-  } else {
-    const size_t sm = train_smem<3>();
-    cudaFuncSetAttribute(k_mlp_train<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_mlp_train<3><<<grid, 32 * WARPS, sm, st>>>(a);
-  }
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_mlp_train: ") + cudaGetErrorString(e));
-  return SL_OK;
-}
-
 sl_status sl_mlp_gradients(sl_mlp* M, const float* noisy, const float* clean, float sigma,
                            const int* idx, int n, float* grad_host, float* loss_host,
                            void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  sl_status s = train_launch(M, noisy, clean, sigma, idx, n, st);
+  sl_status s = train_launch(M, noisy, clean, sigma, idx, n, st, false, 0.f);
   if (s != SL_OK) return s;
   if (grad_host && cudaMemcpyAsync(grad_host, M->grad, M->P * sizeof(float),
                                    cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -1228,17 +1783,11 @@ sl_status sl_mlp_gradients(sl_mlp* M, const float* noisy, const float* clean, fl
 sl_status sl_mlp_train_step(sl_mlp* M, const float* noisy, const float* clean, float sigma,
                             const int* idx, int n, float lr, float* loss_dev, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  sl_status s = train_launch(M, noisy, clean, sigma, idx, n, st);
+  sl_status s = train_launch(M, noisy, clean, sigma, idx, n, st, true, lr);
   if (s != SL_OK) return s;
-  M->t += 1;
-  const float c1 = 1.f - std::pow(0.9f, (float)M->t), c2 = 1.f - std::pow(0.999f, (float)M->t);
-  M->tc_packed = false;
-  k_adam<<<(M->P + 255) / 256, 256, 0, st>>>(M->prm, M->grad, M->m, M->v, M->P, lr, c1, c2);
   if (loss_dev &&
       cudaMemcpyAsync(loss_dev, M->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return mfail(SL_ECUDA, "copy loss");
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return mfail(SL_ECUDA, std::string("k_adam: ") + cudaGetErrorString(e));
   return SL_OK;
 }
 
@@ -1262,11 +1811,7 @@ sl_status sl_mlp_apply(sl_mlp* M, const float* coeffs, float* out, float sigma, 
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return mfail(SL_ECUDA, "cudaStreamIsCapturing");
   const bool repack = !M->tc_packed || M->pack_stream != st || cap != cudaStreamCaptureStatusNone;
   if (M->engine == SL_MLP_TCGEN05) {
-    // Per-tile wait limit in SM cycles: the default (about two seconds), or the value
-    // of SL_MLP_WAIT_CYCLES, a test hook that makes the waits run out on purpose so
-    // that the timeout path (flag, drain, free, sl_mlp_check) can be exercised.
-    long long limit = kTcWaitCycles;
-    if (const char* e = std::getenv("SL_MLP_WAIT_CYCLES")) limit = std::max(0LL, std::atoll(e));
+    const long long limit = tc_wait_limit();
     // the grid keeps every SM's CTAs within its 512 TMEM columns: no allocation waits
     if (M->ndim == 2) {
       const size_t sm = sizeof(TcApplySmem<2>);
@@ -1321,7 +1866,8 @@ sl_status sl_mlp_check(sl_mlp* M, void* stream) {
     return mfail(SL_ECUDA, std::string("sl_mlp_check: ") + cudaGetErrorString(cudaGetLastError()));
   if (h) {
     cudaMemset(M->tc_err, 0, sizeof(int));
-    return mfail(SL_ECUDA, "a tensor-core wait of sl_mlp_apply ran out (its output is incomplete)");
+    return mfail(SL_ECUDA, "a tensor-core wait ran out (the output of sl_mlp_apply, or the "
+                           "gradients of a training call, are incomplete)");
   }
   return SL_OK;
 }

@@ -654,7 +654,8 @@ class MLP:
         return out
 
     def set_engine(self, engine: str):
-        """'tcgen05' (default) or 'mma_sync': the tensor-core path of apply."""
+        """'tcgen05' (default) or 'mma_sync': the tensor-core path of apply, gradients and
+        train_step."""
         if engine not in MLP_ENGINES:
             raise ValueError(f"engine must be one of {sorted(MLP_ENGINES)}")
         _mcheck(lib().sl_mlp_set_engine(self.handle, MLP_ENGINES[engine]), "sl_mlp_set_engine")

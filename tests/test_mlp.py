@@ -119,15 +119,19 @@ def _rel(a, b):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("case", [((64, 64), 2, (1, 1)), ((16, 16, 16), 1, (0,))], ids=str)
-def test_gpu_gradients_match_oracle(case):
+def test_gpu_gradients_match_oracle(case, engine):
     """The tensor-core backward pass against the oracle: within 1e-2 of the oracle with
     the same BF16 operand rounding (FP32 vs FP64 accumulation, rare rounding-boundary
-    flips), and within 5e-2 of the exact FP64 gradients (the BF16 effect itself)."""
+    flips), and within 5e-2 of the exact FP64 gradients (the BF16 effect itself). The
+    tcgen05 engine also rounds the operands of the bias and w3 sums (dz2, dz1, h2, dz3)
+    to BF16, inside the same bounds."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dims, J, sl = case
     b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 3)
+    mlp.set_engine(engine)
     s_sys = oracle_system(dims, J, sl)
     r = np.random.default_rng(5)
     n = 2048
@@ -156,6 +160,71 @@ def test_gpu_gradients_match_oracle(case):
         assert e1 < 1e-2, (k, e1)
         assert e2 < 5e-2, (k, e2)
         off += sz
+    mlp.check()
+
+
+@pytest.mark.gpu
+def test_training_engines_agree_and_descend():
+    """Thirty Adam steps from the same start on the same samples (65,536 per step, 512
+    tiles: several per CTA): the tcgen05 and mma.sync engines give parameters within
+    2e-2 of each other (relative L2 per tensor; BF16 products summed in other orders),
+    and both lower the loss."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dims, J, sl = (256, 256), 3, (1, 1, 2)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 4)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(9)
+    idxs = [(torch.randint(0, (b.R - 1) * b.N, (65536,), generator=gen, device="cuda")
+             + b.N).to(torch.int32) for _ in range(30)]
+    out = {}
+    for engine in ("tcgen05", "mma_sync"):
+        mlp.set_params(flat)
+        mlp.set_engine(engine)
+        loss = torch.zeros(1, device="cuda")
+        hist = []
+        for idx in idxs:
+            mlp.train_step(Cn, Cc, 20.0, idx, 2e-3, loss_out=loss)
+            hist.append(float(loss.item()))
+        mlp.check()
+        assert hist[-1] < 0.9 * hist[0], (engine, hist[0], hist[-1])
+        out[engine] = mlp.get_params().astype(np.float64)
+    off = 0
+    for k, sh in M.param_shapes(2, b.R).items():
+        sz = int(np.prod(sh))
+        a_, c_ = out["tcgen05"][off:off + sz], out["mma_sync"][off:off + sz]
+        assert _rel(a_, c_) < 2e-2, (k, _rel(a_, c_))
+        off += sz
+
+
+@pytest.mark.gpu
+def test_training_wait_timeout_is_reported_and_recovers(monkeypatch):
+    """The tcgen05 trainer's bounded waits, made to run out at once (SL_MLP_WAIT_CYCLES=0,
+    a test hook): the call returns, sl_mlp_check reports the flag and clears it, and
+    the next call with the normal limit gives the gradients from before, exactly except
+    for the embedding's (summed with shared-memory atomics in any order) to 1e-6."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5670_b300.shearlet import ShearletError
+    dims, J, sl = (64, 64), 2, (1, 1)
+    b, mlp, flat, Cn, Cc = _gpu_setup(dims, J, sl, 7)
+    mlp.set_engine("tcgen05")
+    r = np.random.default_rng(3)
+    idx = torch.from_numpy(r.integers(b.N, b.R * b.N, 1024).astype(np.int32)).cuda()
+    L0, g0 = mlp.gradients(Cn, Cc, 20.0, idx)
+    mlp.check()
+    monkeypatch.setenv("SL_MLP_WAIT_CYCLES", "0")
+    mlp.gradients(Cn, Cc, 20.0, idx)
+    with pytest.raises(ShearletError):
+        mlp.check()
+    monkeypatch.delenv("SL_MLP_WAIT_CYCLES")
+    mlp.check()  # the flag was cleared
+    L1, g1 = mlp.gradients(Cn, Cc, 20.0, idx)
+    mlp.check()
+    nE = b.R * M.EMBED
+    assert L1 == L0
+    assert np.array_equal(g1[:-nE], g0[:-nE])
+    assert _rel(g1[-nE:], g0[-nE:]) < 1e-6
 
 
 @pytest.mark.gpu
