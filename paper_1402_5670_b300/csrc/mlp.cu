@@ -718,27 +718,30 @@ static int apply_tc_grid() {
 }
 
 // ---------------------------------------------- training on tcgen05 tensor cores ---
-// One CTA of 4 warps per SM walks tiles of 128 samples (thread t owns row t, TMEM lane
-// t). Per tile, one thread issues five products, each accumulating in tensor memory:
+// One CTA of 8 warps per SM walks tiles of 128 samples; row r of a tile is TMEM lane
+// r, read by warps r / 32 and 4 + r / 32, which split the 64 columns of every layer
+// between them (warps 0-3 take columns 0-31, warps 4-7 columns 32-63). Per tile, one
+// thread issues six products, each accumulating in tensor memory:
 //   z1  = [x, 1, 1] [W1, b1]^T            (128 x 64, K = KP)     -> columns 0..63
 //   z2  = [h1, 1, 1] [W2, b2]^T           (128 x 64, K = K2)     -> columns 0..63
 //   dh1 = dz2 W2                          (128 x 64, K = 64)     -> columns 0..63
-//   D1 += [dz2 ; dz1]^T [x ; h1]          (128 x (KP + 64), K = 128 rows of the tile)
+//   D1 += [dz2 ; dz1]^T [x ; h1]          (128 x (KP + 64), K = the tile's 128 rows)
 //   D2 += [h2 ; x ; h1]^T [dz3, 0 ..]     (128 x 16, K = 128)
-// The last two carry the weight gradients across the CTA's tiles: D1 holds dW2 (dz2
-// rows x h1 columns), dW1 (dz1 rows x feature columns), and through the constant-one
-// feature columns b2's and b1's gradients; D2 holds w3's gradient (h2 rows) and b3's
-// (the one-row of x). The cross blocks (dz2 x features, dz1 x h1, ...) are computed
-// and ignored: they keep both products at M = 128. The gradient of the subband
-// embedding (dx for the embedding features, a 64 x 8 product per row) is summed on the
-// CUDA cores into a per-CTA table in shared memory. At the end every CTA writes its
-// gradients and its loss as one row of a partial-sum table; k_mlp_reduce adds the rows
-// in a fixed order (and applies Adam).
+//   DE  = dz1 [W1 embedding columns, 0 ..] (128 x 16, K = 64)
+// D1 and D2 carry the weight gradients across the CTA's tiles: D1 holds dW2 (dz2 rows x
+// h1 columns), dW1 (dz1 rows x feature columns), and through the constant-one feature
+// column b2's and b1's gradients; D2 holds w3's gradient (h2 rows) and b3's (the
+// one-row of x). The cross blocks (dz2 x features, dz1 x h1, ...) are computed and
+// ignored: they keep both products at M = 128. DE is each row's gradient with respect
+// to its subband embedding, added into a per-CTA table in shared memory (read at the
+// start of the next tile, while that tile's features are built). At the end every CTA
+// writes its gradients and its loss as one row of a partial-sum table; k_mlp_reduce
+// adds the rows in a fixed order (and applies Adam).
 // The weight-gradient operands are K-major over the tile's rows (element (m, r) of a
 // [M][128] tile), written with one 2-byte store per value; their core matrices sit
 // 144 bytes apart along K (128 + 16 of padding) so that the four 8-lane groups of a
 // warp store into different banks.
-constexpr int TT_THREADS = 128;
+constexpr int TT_THREADS = 256;
 constexpr int TT_TMEM_COLS = 256;
 constexpr int KR = 128;                  // rows per tile = K of the weight-gradient products
 constexpr int KR_LBO = 144;              // K-direction core-matrix stride of those operands
@@ -750,16 +753,19 @@ __host__ __device__ __forceinline__ int kmajor_r(int m, int r) {
 
 // Weights of one training CTA: the inference tiles plus W2 transposed (the B operand of
 // dz2 W2: element (i, o) = W2[o][i], K-major over o) and W1's embedding columns
-// rounded to BF16 (as FP32 values, [o][e]).
+// transposed (the B operand of DE: element (e, o) = W1[o][1 + NB + e] for e < 8, zero
+// rows 8..15).
 template <int NDIM>
 struct TcTrainWeights {
   TcWeights<NDIM> base;
   alignas(16) unsigned char w2t[H * H * 2];
-  alignas(16) float w1e[H * EMB];
+  alignas(16) unsigned char w1et[16 * H * 2];
 };
 
 template <int NDIM>
-__host__ __device__ constexpr int tc_train_pack_elems() { return tc_pack_elems<NDIM>() + H * H + H * EMB; }
+__host__ __device__ constexpr int tc_train_pack_elems() {
+  return tc_pack_elems<NDIM>() + H * H + 16 * H;
+}
 
 template <int NDIM>
 __global__ void __launch_bounds__(256) k_mlp_pack_train(const float* __restrict__ prm,
@@ -772,15 +778,16 @@ __global__ void __launch_bounds__(256) k_mlp_pack_train(const float* __restrict_
   }
   i -= tc_pack_elems<NDIM>();
   if (i < H * H) {
-    const int n = i / H, o = i % H;  // W2^T row n = hidden unit i of h1, K index o
+    const int n = i / H, o = i % H;  // row n = hidden unit of h1, K index o
     *reinterpret_cast<__nv_bfloat16*>(out->w2t + kmajor(n, o, H)) =
         __float2bfloat16_rn(prm[NN::oW2 + o * H + n]);
     return;
   }
   i -= H * H;
-  if (i < H * EMB) {
-    const int o = i / EMB, e = i % EMB;
-    out->w1e[i] = __bfloat162float(__float2bfloat16_rn(prm[NN::oW1 + o * NN::F + 1 + NN::NB + e]));
+  if (i < 16 * H) {
+    const int e = i / H, o = i % H;
+    const float w = e < EMB ? prm[NN::oW1 + o * NN::F + 1 + NN::NB + e] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(out->w1et + kmajor(e, o, H)) = __float2bfloat16_rn(w);
   }
 }
 
@@ -789,7 +796,8 @@ struct TcTrainSmem {
   static constexpr int KP = Net<NDIM>::KP;
   static constexpr int TR = 128 + KP;  // rows of tt
   TcTrainWeights<NDIM> w;
-  // features [128][KP], then [h1, 1, 1, 0..] [128][K2], then dz2 [128][64] (K-major)
+  // features [128][KP], then [h1, 1, 1, 0..] [128][K2], then dz2 [128][64], then dz1
+  // [128][64] (K-major)
   alignas(16) unsigned char act[TC_ROWS * K2 * 2];
   alignas(16) unsigned char aw1[(128 / 8) * KR_SBO];  // [dz2^T ; dz1^T]      [128][KR]
   alignas(16) unsigned char tt[(TR / 8) * KR_SBO];    // [h2^T ; x^T ; h1^T]  [TR][KR]
@@ -797,6 +805,8 @@ struct TcTrainSmem {
   alignas(8) uint64_t bar;
   uint32_t tmem;
   float red[TT_THREADS / 32];
+  float z3half[2][TC_ROWS];  // each column half's part of the output dot
+  int jrow[TC_ROWS];         // subband of each row of the tile
   // followed by the CTA's embedding-gradient table, R x EMB floats
 };
 
@@ -818,14 +828,17 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
   constexpr int F = NN::F, KP = NN::KP, NB = NN::NB;
   constexpr int CENTRE = NB / 2;
   constexpr int NW1 = KP + H;                 // columns of D1: features, then h1
-  constexpr int C_D1 = H, C_D2 = H + NW1;     // tensor-memory columns of D1 and D2
-  static_assert(C_D2 + 16 <= TT_TMEM_COLS, "tensor-memory budget");
+  constexpr int C_D1 = H, C_D2 = H + NW1, C_E = C_D2 + 16;  // tensor-memory columns
+  static_assert(C_E + 16 <= TT_TMEM_COLS, "tensor-memory budget");
   static_assert(NW1 % 16 == 0 && NW1 <= 256, "N of the D1 product");
   static_assert(64 + F < 128, "the one-row of x lies inside D2's 128 rows");
   extern __shared__ __align__(16) unsigned char smraw[];
   SM& S = *reinterpret_cast<SM*>(smraw);
   float* sE = reinterpret_cast<float*>(smraw + sizeof(SM));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = warp >> 2;   // column half of every layer: 32 * half ..
+  const int r = tid & 127;      // row of the tile = TMEM lane
+  const int col0 = 32 * half;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&S.tmem)),
@@ -840,10 +853,13 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
   }
   for (int i = tid; i < a.R * EMB; i += TT_THREADS) sE[i] = 0.f;
   // rows that never change: x^T's two bias ones and its zero padding, bw2's zero rows
+  if (half == 0) {
 #pragma unroll
-  for (int k = F; k < KP; ++k) st_bf16(S.tt, kmajor_r(64 + k, tid), k < F + 2 ? 1.f : 0.f);
+    for (int k = F; k < KP; ++k) st_bf16(S.tt, kmajor_r(64 + k, r), k < F + 2 ? 1.f : 0.f);
+  } else {
 #pragma unroll
-  for (int m = 1; m < 16; ++m) st_bf16(S.bw2, kmajor_r(m, tid), 0.f);
+    for (int m = 1; m < 16; ++m) st_bf16(S.bw2, kmajor_r(m, r), 0.f);
+  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -853,65 +869,90 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
   __syncthreads();
   tc_after_sync();
   const uint32_t tmem = S.tmem;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const float* E = a.prm + NN::oE;
   const int lgN = a.geo.lg[0] + a.geo.lg[1] + a.geo.lg[2];
   const int tiles = a.n / TC_ROWS;
   const float inv_n = 1.f / (float)a.n;
   const uint32_t act = smem_addr(S.act), w1 = smem_addr(S.w.base.w1), w2 = smem_addr(S.w.base.w2),
-                 w2t = smem_addr(S.w.w2t), aw1 = smem_addr(S.aw1), tt = smem_addr(S.tt),
-                 bw2 = smem_addr(S.bw2);
+                 w2t = smem_addr(S.w.w2t), w1et = smem_addr(S.w.w1et), aw1 = smem_addr(S.aw1),
+                 tt = smem_addr(S.tt), bw2 = smem_addr(S.bw2);
   constexpr uint32_t kOnes = 0x3F803F80u;  // two BF16 ones
+  const float* w3 = S.w.base.w3;
   // sample indices are clamped to subbands 1..R-1 so that a bad index cannot read
   // outside the stacks (the API requires valid indices)
   const int64_t qlo = a.geo.N, qhi = (int64_t)a.R * a.geo.N - 1;
-  float nb[NB];
-  float cc_next = 0.f;
+  float nb[NB];  // row r's neighbourhood (the first half's threads), loaded a tile ahead
+#pragma unroll
+  for (int d = 0; d < NB; ++d) nb[d] = 0.f;
+  float cc_next = 0.f, is_next = 0.f, e_next[EMB];
+#pragma unroll
+  for (int e = 0; e < EMB; ++e) e_next[e] = 0.f;
   int64_t q_next = qlo;
-  auto gather = [&](int t) {  // this thread's sample of tile t, loaded a tile ahead
+  auto gather = [&](int t) {  // with the row's 1/s and (first half) its embedding
     if (t < tiles) {
-      const int64_t q = min(max((int64_t)__ldg(a.idx + (int64_t)t * TC_ROWS + tid), qlo), qhi);
+      const int64_t q = min(max((int64_t)__ldg(a.idx + (int64_t)t * TC_ROWS + r), qlo), qhi);
+      const int jn = (int)(q >> lgN);
       q_next = q;
-      gather_nb<NDIM>(a.geo, a.C + ((q >> lgN) << lgN), (uint32_t)(q & (a.geo.N - 1)), nb);
+      if (half == 0) {
+        gather_nb<NDIM>(a.geo, a.C + ((q >> lgN) << lgN), (uint32_t)(q & (a.geo.N - 1)), nb);
+#pragma unroll
+        for (int e = 0; e < EMB; ++e) e_next[e] = ld_early(E + jn * EMB + e);
+      } else {
+        nb[CENTRE] = ld_early(a.C + q);
+      }
       cc_next = ld_early(a.Cc + q);
+      is_next = ld_early(a.inv_s + jn);
     }
   };
   gather(blockIdx.x);
   // The mbarrier completes four phases per tile: layer 1 (parity 0), layer 2 (1), dh1
-  // (0), the weight-gradient products (1, waited for at the next tile's start). A wait
-  // that runs out is made CTA-uniform at the next barrier and ends the loop there.
+  // (0), the gradient products (1, waited for at the next tile's start). A wait that
+  // runs out is made CTA-uniform at the next barrier and ends the loop there.
   float loss_acc = 0.f;
+  int jprev = 0;         // subband of row r in the previous tile (second half)
   int timed_out = 0;     // CTA-uniform
   uint32_t pending = 0;  // parity of the phase a timed-out wait left in flight
   bool late = false;     // this warp's last wait ran out (warp-uniform)
-  bool first = true;     // no weight-gradient product issued yet (CTA-uniform)
+  bool first = true;     // no gradient product issued yet (CTA-uniform)
+  // the previous tile's embedding gradients (DE) into the CTA's table
+  auto take_de = [&]() {
+    float v[16];
+    tmem_ld16(tmem + lane_base + C_E, v);
+#pragma unroll
+    for (int e = 0; e < EMB; ++e) atomicAdd(sE + jprev * EMB + e, v[e]);
+  };
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    // the previous tile's weight-gradient products read aw1, tt and bw2
+    // the previous tile's gradient products read aw1, tt, bw2 and act
     if (!first) late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
     tc_after_sync();
     const int64_t q = q_next;
     const int j = (int)(q >> lgN);
     const float c = nb[CENTRE], cc = cc_next;
-    const float is = a.inv_s[j];
+    const float is = is_next;
     if (!late) {
-      float x[KP];
-      x[0] = c * is;
+      if (half == 0) {
+        float x[KP];
+        x[0] = c * is;
 #pragma unroll
-      for (int d = 0; d < NB; ++d) x[1 + d] = fabsf(nb[d]) * is;
+        for (int d = 0; d < NB; ++d) x[1 + d] = fabsf(nb[d]) * is;
 #pragma unroll
-      for (int e = 0; e < EMB; ++e) x[1 + NB + e] = __ldg(E + j * EMB + e);
-      x[F] = 1.f;
-      x[F + 1] = 1.f;
+        for (int e = 0; e < EMB; ++e) x[1 + NB + e] = e_next[e];
+        x[F] = 1.f;
+        x[F + 1] = 1.f;
 #pragma unroll
-      for (int k = F + 2; k < KP; ++k) x[k] = 0.f;
+        for (int k = F + 2; k < KP; ++k) x[k] = 0.f;
 #pragma unroll
-      for (int k8 = 0; k8 < KP / 8; ++k8)
-        *reinterpret_cast<uint4*>(S.act + kmajor(tid, 8 * k8, KP)) =
-            make_uint4(pack_bf16(x[8 * k8], x[8 * k8 + 1]), pack_bf16(x[8 * k8 + 2], x[8 * k8 + 3]),
-                       pack_bf16(x[8 * k8 + 4], x[8 * k8 + 5]),
-                       pack_bf16(x[8 * k8 + 6], x[8 * k8 + 7]));
+        for (int k8 = 0; k8 < KP / 8; ++k8)
+          *reinterpret_cast<uint4*>(S.act + kmajor(r, 8 * k8, KP)) =
+              make_uint4(pack_bf16(x[8 * k8], x[8 * k8 + 1]), pack_bf16(x[8 * k8 + 2], x[8 * k8 + 3]),
+                         pack_bf16(x[8 * k8 + 4], x[8 * k8 + 5]),
+                         pack_bf16(x[8 * k8 + 6], x[8 * k8 + 7]));
 #pragma unroll
-      for (int k = 0; k < F; ++k) st_bf16(S.tt, kmajor_r(64 + k, tid), x[k]);
+        for (int k = 0; k < F; ++k) st_bf16(S.tt, kmajor_r(64 + k, r), x[k]);
+      } else if (!first) {
+        take_de();
+      }
     }
     fence_async_smem();
     tc_before_sync();
@@ -931,26 +972,25 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     }
     late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0, wait_limit));
     tc_after_sync();
-    uint32_t mask[2] = {0u, 0u};  // z1 > 0
+    uint32_t mask = 0u;  // z1 > 0 on this half's columns
     if (!late) {
+      float z[32];
+      tmem_ld32(tmem + lane_base + col0, z);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float z[32];
-        tmem_ld32(tmem + lane_base + 32 * h, z);
+      for (int i = 0; i < 32; ++i) mask |= (z[i] > 0.f ? 1u : 0u) << i;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) mask[h] |= (z[i] > 0.f ? 1u : 0u) << i;
+      for (int k8 = 0; k8 < 4; ++k8)
+        *reinterpret_cast<uint4*>(S.act + kmajor(r, col0 + 8 * k8, K2)) =
+            make_uint4(relu_pack_bf16(z[8 * k8], z[8 * k8 + 1]),
+                       relu_pack_bf16(z[8 * k8 + 2], z[8 * k8 + 3]),
+                       relu_pack_bf16(z[8 * k8 + 4], z[8 * k8 + 5]),
+                       relu_pack_bf16(z[8 * k8 + 6], z[8 * k8 + 7]));
 #pragma unroll
-        for (int k8 = 0; k8 < 4; ++k8)
-          *reinterpret_cast<uint4*>(S.act + kmajor(tid, 32 * h + 8 * k8, K2)) =
-              make_uint4(relu_pack_bf16(z[8 * k8], z[8 * k8 + 1]),
-                         relu_pack_bf16(z[8 * k8 + 2], z[8 * k8 + 3]),
-                         relu_pack_bf16(z[8 * k8 + 4], z[8 * k8 + 5]),
-                         relu_pack_bf16(z[8 * k8 + 6], z[8 * k8 + 7]));
-#pragma unroll
-        for (int i = 0; i < 32; ++i) st_bf16(S.tt, kmajor_r(64 + KP + 32 * h + i, tid), fmaxf(z[i], 0.f));
+      for (int i = 0; i < 32; ++i) st_bf16(S.tt, kmajor_r(64 + KP + col0 + i, r), fmaxf(z[i], 0.f));
+      if (half == 0) {
+        *reinterpret_cast<uint4*>(S.act + kmajor(r, H, K2)) = make_uint4(kOnes, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(S.act + kmajor(r, H + 8, K2)) = make_uint4(0u, 0u, 0u, 0u);
       }
-      *reinterpret_cast<uint4*>(S.act + kmajor(tid, H, K2)) = make_uint4(kOnes, 0u, 0u, 0u);
-      *reinterpret_cast<uint4*>(S.act + kmajor(tid, H + 8, K2)) = make_uint4(0u, 0u, 0u, 0u);
     }
     fence_async_smem();
     tc_before_sync();
@@ -971,46 +1011,46 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     }
     late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
     tc_after_sync();
+    float z[32];
     if (!late) {
-      float za[32], zb[32];
-      tmem_ld32(tmem + lane_base, za);
-      tmem_ld32(tmem + lane_base + 32, zb);
-      const float* w3 = S.w.base.w3;
-      float acc[4] = {S.w.base.b3[0], 0.f, 0.f, 0.f};
+      tmem_ld32(tmem + lane_base + col0, z);
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < 32; i += 4) {
-        acc[0] += fmaxf(za[i], 0.f) * w3[i] + fmaxf(zb[i], 0.f) * w3[32 + i];
-        acc[1] += fmaxf(za[i + 1], 0.f) * w3[i + 1] + fmaxf(zb[i + 1], 0.f) * w3[33 + i];
-        acc[2] += fmaxf(za[i + 2], 0.f) * w3[i + 2] + fmaxf(zb[i + 2], 0.f) * w3[34 + i];
-        acc[3] += fmaxf(za[i + 3], 0.f) * w3[i + 3] + fmaxf(zb[i + 3], 0.f) * w3[35 + i];
+        acc[0] += fmaxf(z[i], 0.f) * w3[col0 + i];
+        acc[1] += fmaxf(z[i + 1], 0.f) * w3[col0 + i + 1];
+        acc[2] += fmaxf(z[i + 2], 0.f) * w3[col0 + i + 2];
+        acc[3] += fmaxf(z[i + 3], 0.f) * w3[col0 + i + 3];
       }
-      const float g = 1.f / (1.f + expf(-((acc[0] + acc[1]) + (acc[2] + acc[3]))));
+      S.z3half[half][r] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+    __syncthreads();  // both halves of the output dot
+    if (!late) {
+      const float g =
+          1.f / (1.f + expf(-(S.w.base.b3[0] + (S.z3half[0][r] + S.z3half[1][r]))));
       const float res = (g * c - cc) * is;
-      loss_acc += res * res;
       const float dz3 = 2.f * res * c * is * inv_n * g * (1.f - g);
-      float dz2[H];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        dz2[i] = za[i] > 0.f ? dz3 * w3[i] : 0.f;
-        dz2[32 + i] = zb[i] > 0.f ? dz3 * w3[32 + i] : 0.f;
+      if (half == 0) {
+        loss_acc += res * res;
+        st_bf16(S.bw2, kmajor_r(0, r), dz3);
       }
-      // dz2 as the A operand of dh1 (act is free: layer 2 is done) and as rows of aw1;
-      // h2 as rows of tt; dz3 as the one live row of bw2
+      // dz2 on this half's columns: the A operand of dh1 (act is free: layer 2 is
+      // done) and rows of aw1; h2 as rows of tt
+      float dz2[32];
 #pragma unroll
-      for (int k8 = 0; k8 < H / 8; ++k8)
-        *reinterpret_cast<uint4*>(S.act + kmajor(tid, 8 * k8, H)) =
+      for (int i = 0; i < 32; ++i) dz2[i] = z[i] > 0.f ? dz3 * w3[col0 + i] : 0.f;
+#pragma unroll
+      for (int k8 = 0; k8 < 4; ++k8)
+        *reinterpret_cast<uint4*>(S.act + kmajor(r, col0 + 8 * k8, H)) =
             make_uint4(pack_bf16(dz2[8 * k8], dz2[8 * k8 + 1]),
                        pack_bf16(dz2[8 * k8 + 2], dz2[8 * k8 + 3]),
                        pack_bf16(dz2[8 * k8 + 4], dz2[8 * k8 + 5]),
                        pack_bf16(dz2[8 * k8 + 6], dz2[8 * k8 + 7]));
 #pragma unroll
-      for (int i = 0; i < H; ++i) st_bf16(S.aw1, kmajor_r(i, tid), dz2[i]);
-#pragma unroll
       for (int i = 0; i < 32; ++i) {
-        st_bf16(S.tt, kmajor_r(i, tid), fmaxf(za[i], 0.f));
-        st_bf16(S.tt, kmajor_r(32 + i, tid), fmaxf(zb[i], 0.f));
+        st_bf16(S.aw1, kmajor_r(col0 + i, r), dz2[i]);
+        st_bf16(S.tt, kmajor_r(col0 + i, r), fmaxf(z[i], 0.f));
       }
-      st_bf16(S.bw2, kmajor_r(0, tid), dz3);
     }
     fence_async_smem();
     tc_before_sync();
@@ -1031,35 +1071,24 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 0, wait_limit));
     tc_after_sync();
     if (!late) {
-      // dz1 = dh1 [z1 > 0], rounded to BF16 as the products see it; rows of aw1; and
-      // the embedding gradient dz1 W1[:, embedding] into the CTA's table
-      float ge[EMB];
+      // dz1 = dh1 [z1 > 0], rounded to BF16 as the products see it: rows of aw1 and
+      // the A operand of DE (act is free: dh1 is done)
+      tmem_ld32(tmem + lane_base + col0, z);
+      uint32_t pk[16];
 #pragma unroll
-      for (int e = 0; e < EMB; ++e) ge[e] = 0.f;
-      const float4* w1e = reinterpret_cast<const float4*>(S.w.w1e);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float d[32];
-        tmem_ld32(tmem + lane_base + 32 * h, d);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int o = 32 * h + i;
-          const __nv_bfloat16 vb = __float2bfloat16_rn((mask[h] >> i) & 1u ? d[i] : 0.f);
-          *reinterpret_cast<__nv_bfloat16*>(S.aw1 + kmajor_r(64 + o, tid)) = vb;
-          const float v = __bfloat162float(vb);
-          const float4 wa = w1e[2 * o], wb = w1e[2 * o + 1];
-          ge[0] += v * wa.x;
-          ge[1] += v * wa.y;
-          ge[2] += v * wa.z;
-          ge[3] += v * wa.w;
-          ge[4] += v * wb.x;
-          ge[5] += v * wb.y;
-          ge[6] += v * wb.z;
-          ge[7] += v * wb.w;
-        }
+      for (int i = 0; i < 32; i += 2) {
+        const float v0 = (mask >> i) & 1u ? z[i] : 0.f;
+        const float v1 = (mask >> (i + 1)) & 1u ? z[i + 1] : 0.f;
+        pk[i / 2] = pack_bf16(v0, v1);
+        const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162*>(&pk[i / 2]);
+        *reinterpret_cast<__nv_bfloat16*>(S.aw1 + kmajor_r(64 + col0 + i, r)) = p2.x;
+        *reinterpret_cast<__nv_bfloat16*>(S.aw1 + kmajor_r(64 + col0 + i + 1, r)) = p2.y;
       }
 #pragma unroll
-      for (int e = 0; e < EMB; ++e) atomicAdd(sE + j * EMB + e, ge[e]);
+      for (int k8 = 0; k8 < 4; ++k8)
+        *reinterpret_cast<uint4*>(S.act + kmajor(r, col0 + 8 * k8, H)) =
+            make_uint4(pk[4 * k8], pk[4 * k8 + 1], pk[4 * k8 + 2], pk[4 * k8 + 3]);
+      if (half == 0) S.jrow[r] = j;
     }
     fence_async_smem();
     tc_before_sync();
@@ -1069,7 +1098,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
       break;
     }
     tc_after_sync();
-    // D1 += [dz2 ; dz1]^T [x ; h1],  D2 += [h2 ; x ; h1]^T [dz3, 0 ..]
+    if (half == 1) jprev = S.jrow[r];
+    // D1 += [dz2 ; dz1]^T [x ; h1],  D2 += [h2 ; x ; h1]^T [dz3, 0 ..],  DE = dz1 W1e^T
     if (tid == 0) {
 #pragma unroll
       for (int ks = 0; ks < KR / 16; ++ks)
@@ -1081,6 +1111,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         umma_bf16(tmem + C_D2, umma_desc(tt + ks * 2 * KR_LBO, KR_LBO, KR_SBO),
                   umma_desc(bw2 + ks * 2 * KR_LBO, KR_LBO, KR_SBO),
                   (!first || ks > 0) ? 1u : 0u, idesc_m128(16));
+#pragma unroll
+      for (int ks = 0; ks < H / 16; ++ks)
+        umma_bf16(tmem + C_E, umma_desc(act + ks * 256, 128, (H / 8) * 128),
+                  umma_desc(w1et + ks * 256, 128, (H / 8) * 128), ks > 0, idesc_m128(16));
       umma_commit(&S.bar);
     }
     first = false;
@@ -1088,6 +1122,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
   if (!timed_out && !first) {
     late = __any_sync(0xffffffffu, !mbar_wait(&S.bar, 1, wait_limit));
     tc_after_sync();
+    if (!late && half == 1) take_de();
     if (__syncthreads_or(late)) {
       timed_out = 1;
       pending = 1;
@@ -1107,12 +1142,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
   } else {
     // this CTA's row of the partial-sum table: every gradient entry and the loss
     float* row = parts + (size_t)blockIdx.x * stride;
-    const int m = tid;  // TMEM lane = row of D1 and D2
-    if (first) {        // no tile: zero gradients
+    const int m = r;  // TMEM lane = row of D1 and D2
+    if (first) {      // no tile: zero gradients
       for (int i = tid; i < NN::oE; i += TT_THREADS) row[i] = 0.f;
     } else {
-#pragma unroll
-      for (int c0 = 0; c0 < NW1; c0 += 16) {
+      for (int c0 = 16 * half; c0 < NW1; c0 += 32) {  // the halves take alternate chunks
         float v[16];
         tmem_ld16(tmem + lane_base + C_D1 + c0, v);
 #pragma unroll
@@ -1128,10 +1162,12 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
           }
         }
       }
-      float v[16];
-      tmem_ld16(tmem + lane_base + C_D2, v);
-      if (m < H) row[NN::ow3 + m] = v[0];
-      if (m == H + F) row[NN::ob3] = v[0];
+      if (half == 0) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + C_D2, v);
+        if (m < H) row[NN::ow3 + m] = v[0];
+        if (m == H + F) row[NN::ob3] = v[0];
+      }
     }
     float l = loss_acc;
 #pragma unroll

@@ -337,9 +337,11 @@ def test_tensor_core_wait_timeout_is_reported_and_recovers(monkeypatch):
 
 @pytest.mark.gpu
 def test_learned_shrinkage_beats_hard_thresholding():
-    """Trained on the GPU from transform-generated pairs, the learned gain must denoise
-    held-out synthetic images better (PSNR) than the paper's hard threshold at every
-    tested noise level."""
+    """Trained on the GPU from transform-generated pairs (20,000 Adam steps of 65,536
+    samples on 12 cartoons x 4 noise levels), the learned gain must denoise held-out
+    synthetic images better (PSNR) than the paper's hard threshold at every tested
+    noise level: each gain above 0.08 dB and their mean above 0.2 dB (measured on a
+    B300: 0.16 to 0.41 dB, mean 0.28)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1402_5670_b300 import learned
@@ -348,8 +350,8 @@ def test_learned_shrinkage_beats_hard_thresholding():
     b = Bank(dims, J, sl, device=0)
     mlp = MLP(b)
     mlp.set_params(synth.mlp_init(2, b.R, 11))
-    pairs = learned.make_pairs(b, [10.0, 20.0, 30.0, 40.0], seeds=[100, 101, 102, 103, 104, 105])
-    hist = learned.train(mlp, pairs, steps=6000, batch=32768, lr=3e-3, seed=1)
+    pairs = learned.make_pairs(b, [10.0, 20.0, 30.0, 40.0], seeds=list(range(100, 112)))
+    hist = learned.train(mlp, pairs, steps=20000, batch=65536, lr=2e-3, seed=1)
     assert hist[-1] < hist[0]
     K = [2.5, 3.8]
     gains = []
@@ -362,8 +364,8 @@ def test_learned_shrinkage_beats_hard_thresholding():
             lrn = mlp.denoise(xg, sg).cpu().numpy()
             gains.append(O.psnr(clean, lrn) - O.psnr(clean, hard))
     print("PSNR gain of learned over hard thresholding (dB):", np.round(gains, 2))
-    assert min(gains) > 0.0
-    assert float(np.mean(gains)) > 0.1
+    assert min(gains) > 0.08
+    assert float(np.mean(gains)) > 0.2
 
 
 @pytest.mark.gpu
