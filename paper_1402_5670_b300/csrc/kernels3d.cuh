@@ -263,7 +263,10 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p, int nslots) 
 //     half spectra (RT keeps each chunk's thresholded rows in the chunk's own part of the
 //     plane buffer until their forward row FFT).
 // Modes as k_plane (ROW_C2R, ROW_R2C, ROW_RT); spectra tile-major (p.tm), real planes
-// row-major.
+// row-major. Input half planes arrive by 16-byte cp.async copies (pairs of elements
+// never straddle a tile run: TC is even); in ROW_C2R mode the next plane's copies are
+// issued into each half of the plane buffer as soon as that half has been consumed, so
+// they overlap the rest of the current plane.
 constexpr int kBigThreads = 768;
 
 template <int L>
@@ -283,10 +286,15 @@ struct BigPlane {
 
 // FFT along axis 1 of columns [c0, c0 + cw) of the half plane P (in place through W).
 // If out is not null the transformed columns go to the tile-major spectrum out (plane
-// i0) instead of back into P. Ends with a CTA barrier.
-template <int L, int DIR>
+// i0) instead of back into P; then `consumed` runs once the chunk's columns of P have
+// been read (after the barrier between the two passes). Ends with a CTA barrier.
+struct NoHook {
+  __device__ void operator()() const {}
+};
+template <int L, int DIR, typename Hook = NoHook>
 __device__ __forceinline__ void big_col_chunk(float2* P, float2* W, int c0, int cw,
-                                              float2* out, const TileMap& tm, int i0) {
+                                              float2* out, const TileMap& tm, int i0,
+                                              Hook consumed = Hook()) {
   using G = BigPlane<L>;
   constexpr int A = G::A, B = G::B, NH = G::NH;
   const float2* tw = g_twiddle + twiddle_offset(L);
@@ -302,6 +310,7 @@ __device__ __forceinline__ void big_col_chunk(float2* P, float2* W, int c0, int 
     for (int kb = 0; kb < B; ++kb) W[(kb * A + a) * cw + c] = v[kb];
   }
   __syncthreads();
+  if (out) consumed();
   for (int it = threadIdx.x; it < cw * B; it += kBigThreads) {
     const int c = it % cw, kb = it / cw;
     float2 w[A];
@@ -318,6 +327,16 @@ __device__ __forceinline__ void big_col_chunk(float2* P, float2* W, int c0, int 
   __syncthreads();
 }
 
+// cp.async copies of elements [e0, e1) (even bounds) of plane i0 of the tile-major half
+// spectrum `in` into P, one 16-byte pair per copy; committed as one group.
+template <int L>
+__device__ __forceinline__ void big_load(float2* P, const float2* in, const TileMap& tm, int i0,
+                                         int e0, int e1) {
+  for (int e = e0 + 2 * (int)threadIdx.x; e < e1; e += 2 * kBigThreads)
+    cp_async16(P + e, in + tm.at(i0, e));
+  cp_async_commit();
+}
+
 template <int L, int MODE>
 __global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nslots) {
   using G = BigPlane<L>;
@@ -330,13 +349,19 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nsl
   const int nitems = nslots * L0;
   const float2* tw = g_twiddle + twiddle_offset(L);
 
+  static_assert(G::HALF % 2 == 0 && (2 * QC * NH) % 2 == 0, "copies move element pairs");
+  bool prefetched = false;  // this item's plane was copied during the previous one
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int slot = item / L0, i0 = item % L0;
     __syncthreads();  // the previous plane is done with P and W
     if constexpr (MODE == ROW_C2R || MODE == ROW_RT) {
-      const float2* in = p.in_half + (int64_t)slot * p.in_stride;
-      for (int i = tid; i < G::HALF; i += kBigThreads) P[i] = in[p.tm.at(i0, i)];
+      if (!prefetched)
+        big_load<L>(P, p.in_half + (int64_t)slot * p.in_stride, p.tm, i0, 0, G::HALF);
+      cp_async_wait<0>();
       __syncthreads();
+      const int next = item + gridDim.x;  // C2R: its plane is copied half by half below
+      const bool pre = MODE == ROW_C2R && next < nitems;
+      const float2* in_next = p.in_half + (int64_t)(next / L0) * p.in_stride;
       for (int c0 = 0; c0 < NH; c0 += CW) big_col_chunk<L, 1>(P, W, c0, min(CW, NH - c0), nullptr, p.tm, i0);
       const float thr = p.use_thr ? p.thr.v[slot] : 0.f;
       float* outr = nullptr;
@@ -369,6 +394,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nsl
           for (int kb = 0; kb < B; ++kb) W[qq * LS + kb * (A + 1) + a] = u[kb];
         }
         __syncthreads();  // the chunk's half rows are consumed: its part of P is free
+        if (pre) big_load<L>(P, in_next, p.tm, next % L0, (2 * q0) * NH, (2 * q0 + 2 * QC) * NH);
         float2* nat = P + (2 * q0) * NH;  // RT: the chunk's natural pairs [QC][L]
         for (int it = tid; it < QC * B; it += kBigThreads) {
           const int kb = it % B, qq = it / B, q = q0 + qq;
@@ -394,22 +420,43 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nsl
         }
         __syncthreads();  // W free for the next chunk
       }
+      prefetched = pre;
       if constexpr (MODE == ROW_C2R) continue;
     }
 
-    // real row pairs (from global for R2C, from each chunk's natural pairs in P for RT)
-    // -> half rows in P -> FFT along axis 1 -> out
+    // real row pairs (R2C: staged from global into each chunk's own part of P, both
+    // chunks' copies issued at once so the second's overlap the first chunk; RT: each
+    // chunk's natural pairs in P) -> half rows in P -> FFT along axis 1 -> out
+    // copies of plane (sl, pl)'s real rows into the chunks' parts of P, one group per chunk
+    auto stage_rows = [&](int sl, int pl) {
+      const float* inr = p.in_real + (int64_t)sl * p.in_stride + (int64_t)pl * (L * L);
+      for (int q0 = 0; q0 < L / 2; q0 += QC) {
+        float* dst = reinterpret_cast<float*>(P + (2 * q0) * NH);
+        const float* src = inr + (2 * q0) * L;
+        for (int o = 4 * tid; o < 2 * QC * L; o += 4 * kBigThreads) cp_async16(dst + o, src + o);
+        cp_async_commit();
+      }
+    };
+    if constexpr (MODE == ROW_R2C) {
+      static_assert(2 * QC * L * 4 <= 2 * QC * NH * 8, "a chunk's real rows fit its part of P");
+      if (!prefetched) stage_rows(slot, i0);
+    }
     for (int q0 = 0; q0 < L / 2; q0 += QC) {
       float2* chunk = P + (2 * q0) * NH;  // the chunk's part of P
+      if constexpr (MODE == ROW_R2C) {
+        if (q0 == 0) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();  // the chunk's real rows have landed
+      }
       for (int it = tid; it < QC * A; it += kBigThreads) {
-        const int a = it % A, qq = it / A, q = q0 + qq;
+        const int a = it % A, qq = it / A;
         float2 v[B];
         if constexpr (MODE == ROW_R2C) {
-          const float* inr = p.in_real + (int64_t)slot * p.in_stride + (int64_t)i0 * (L * L);
+          const float* rows = reinterpret_cast<const float*>(chunk);  // [2 QC][L]
 #pragma unroll
           for (int b = 0; b < B; ++b) {
             const int n = a + A * b;
-            v[b] = make_float2(inr[(2 * q) * L + n], inr[(2 * q + 1) * L + n]);
+            v[b] = make_float2(rows[(2 * qq) * L + n], rows[(2 * qq + 1) * L + n]);
           }
         } else {
 #pragma unroll
@@ -446,7 +493,16 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nsl
       __syncthreads();
     }
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
-    for (int c0 = 0; c0 < NH; c0 += CW) big_col_chunk<L, -1>(P, W, c0, min(CW, NH - c0), out, p.tm, i0);
+    const int next = item + gridDim.x;
+    // R2C: the next plane's rows are staged once the last column chunk has read P
+    const bool pre = MODE == ROW_R2C && next < nitems;
+    for (int c0 = 0; c0 < NH; c0 += CW) {
+      const bool last = c0 + CW >= NH;
+      big_col_chunk<L, -1>(P, W, c0, min(CW, NH - c0), out, p.tm, i0, [&]() {
+        if (pre && last) stage_rows(next / L0, next % L0);
+      });
+    }
+    prefetched = pre;
   }
 }
 
