@@ -3,16 +3,16 @@
 // subband embedding, replacing the hard threshold of the paper's denoiser
 // (eq. hard_tresholding, Sec. 5.3). Training (forward, backward, Adam) and inference
 // run in these kernels; the products run on the tensor cores in BF16 with FP32
-// accumulation (training: warp-level mma.sync with the activations in registers;
-// inference: tcgen05.mma on 128-row tiles with the accumulators in tensor memory, or
-// mma.sync as a second engine), master weights stay FP32.
+// accumulation: tcgen05.mma on 128-row tiles with the accumulators in tensor memory
+// (the default engine, training and inference), or warp-level mma.sync with the
+// activations in registers (the second engine); master weights stay FP32.
 //
 // Network (F = 1 + 3^ndim + 8 features, padded to KP = F rounded up to 16):
 //   x = [c/s, |c(m+d)|/s for d in {-1,0,1}^ndim (row-major, periodic), E_j]
 //   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), g = sigmoid(w3 . h2 + b3), c_hat = g c
 // with s = sigma ||psi_j||_2. Loss on a sample: mean(((g c - c_clean) / s)^2).
 //
-// Tiles: a warp handles 16 coefficients (the M = 16 rows of m16n8k16); the hidden
+// mma.sync engine tiles: a warp handles 16 coefficients (the M = 16 rows of m16n8k16); the hidden
 // width 64 is 8 n-tiles of 8. Fragment layouts (lane = 4 * gid + tig):
 //   A 16x16: a0 = (gid, 2tig..+1), a1 = (gid+8, 2tig..+1), a2 = (gid, 2tig+8..+9),
 //            a3 = (gid+8, 2tig+8..+9);   B 16x8: b0 = (k 2tig..+1, n gid), b1 = (k 2tig+8..+9, n gid)
