@@ -76,7 +76,9 @@ CASES = [((64, 64), 3, (0, 1, 1), False), ((64, 32), 2, (1, 1), False),
          ((16, 16, 16), 2, (0, 1), False), ((32, 16, 8), 2, (1, 1), False),
          ((16, 16, 16), 1, (1,), True), ((384, 64), 2, (1, 1), False),
          ((64, 384), 3, (0, 1, 1), False), ((16, 192, 192), 2, (0, 1), False),
-         ((192, 16, 8), 1, (1,), False)]
+         ((192, 16, 8), 1, (1,), False),
+         # shear level 3 in 2D (refinement by 8, R = 49) and level 2 in 3D (R = 243)
+         ((64, 64), 2, (2, 3), False), ((32, 32, 32), 2, (1, 2), False)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=str)

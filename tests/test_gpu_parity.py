@@ -58,10 +58,10 @@ def cuda(a):
 
 CASES_2D = [((16, 16), 1, (1,)), ((32, 32), 2, (0, 1)), ((64, 32), 2, (1, 1)),
             ((32, 128), 2, (1, 2)), ((128, 256), 3, (1, 1, 2)), ((256, 256), 2, (1, 1)),
-            ((8, 8), 1, (0,)), ((1024, 64), 2, (1, 1))]
+            ((8, 8), 1, (0,)), ((1024, 64), 2, (1, 1)), ((64, 64), 2, (2, 3))]
 CASES_3D = [((8, 8, 8), 1, (0,)), ((16, 16, 16), 2, (0, 1)), ((32, 16, 8), 2, (1, 1)),
             ((16, 32, 64), 2, (1, 1)), ((64, 64, 64), 3, (0, 0, 1)),
-            ((16, 192, 192), 2, (0, 1)), ((192, 32, 16), 2, (1, 1))]
+            ((16, 192, 192), 2, (0, 1)), ((192, 32, 16), 2, (1, 1)), ((32, 32, 32), 2, (1, 2))]
 CASES = CASES_2D + CASES_3D
 
 
