@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p, int nslots) 
         for (int b = 0; b < B; ++b)
           v[r][b] = it < PAIRS * A ? P[q * L2 + a + A * b] : make_float2(0.f, 0.f);
       }
+      if (next < nitems) gather(next, ld);  // in flight during the forward half
     } else {
       __syncthreads();  // the previous item is done with the shared buffers
     }
@@ -243,11 +244,8 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p, int nslots) 
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
     for (int i = tid; i < G::HALF; i += kPlaneThreads) out[p.tm.at(i0, i)] = W[i];
     if constexpr (MODE == ROW_RT) {
-      __syncthreads();  // W read out before the next plane is parked in P... and W
-      if (next < nitems) {
-        gather(next, ld);
-        park(ld);
-      }
+      __syncthreads();  // P is free once the last axis-1 pass has read it
+      if (next < nitems) park(ld);
     }
   }
 }
@@ -494,12 +492,19 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_plane_big(RowArgs p, int nsl
     }
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
     const int next = item + gridDim.x;
-    // R2C: the next plane's rows are staged once the last column chunk has read P
-    const bool pre = MODE == ROW_R2C && next < nitems;
+    // the next plane's input is copied once the last column chunk has read P: R2C its
+    // real rows, RT its half spectrum
+    const bool pre = MODE != ROW_C2R && next < nitems;
     for (int c0 = 0; c0 < NH; c0 += CW) {
       const bool last = c0 + CW >= NH;
       big_col_chunk<L, -1>(P, W, c0, min(CW, NH - c0), out, p.tm, i0, [&]() {
-        if (pre && last) stage_rows(next / L0, next % L0);
+        if (pre && last) {
+          if constexpr (MODE == ROW_R2C)
+            stage_rows(next / L0, next % L0);
+          else
+            big_load<L>(P, p.in_half + (int64_t)(next / L0) * p.in_stride, p.tm, next % L0, 0,
+                        G::HALF);
+        }
       });
     }
     prefetched = pre;
