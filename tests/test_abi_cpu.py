@@ -123,3 +123,26 @@ def test_library_bank_matches_oracle_at_384():
     assert abs(b.A - s.A) <= 1e-12
     b.close()
 
+
+
+def test_library_bank_matches_oracle_at_shear_level_4():
+    """The maximum shear level (refinement by 16, R = 65 on 64 x 64): the library's
+    closed-form bank against values the oracle's spatial construction wrote to
+    tests/golden/shear4_bank_64x64.json (make_shear4_bank.py; the oracle build takes
+    minutes): order, norms, frame bound A and 12 sampled spectrum values per filter,
+    each to 1e-12."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "shear4_bank_64x64.json")) as f:
+        g = json.load(f)
+    b = S.Bank(tuple(g["dims"]), g["nScales"], tuple(g["shearLevels"]), device=-1)
+    assert b.R == g["R"] == len(g["filters"])
+    assert abs(b.A - g["A"]) <= 1e-12
+    for j, fl in enumerate(g["filters"]):
+        assert b.scale_of[j] == fl["scale"] and b.cone_of[j] == fl["cone"]
+        assert tuple(b.k_of[j][:len(fl["k"])]) == tuple(fl["k"])
+        assert abs(b.norms[j] - fl["norm"]) <= 1e-12
+        ph = b.eval_f64(j)
+        for k0, k1, v in fl["samples"]:
+            assert abs(ph[k0, k1] - v) <= 1e-12, (j, k0, k1)
+    b.close()
