@@ -349,3 +349,29 @@ def test_misaligned_arrays_are_rejected_on_the_host():
     st = S.lib().sl_inverse(b.handle, cbuf.data_ptr() + 8, buf.data_ptr(), None)
     assert S.STATUS[st] == "SL_EINVAL"
     torch.cuda.synchronize()
+
+
+@pytest.mark.gpu
+def test_shear_level_4_transform_matches_stored_oracle_spectra():
+    """The maximum shear level on the GPU (64 x 64, R = 65): the forward transform of a
+    unit impulse at the origin has DFT(C_j) = psi_hat_j, so the GPU coefficients,
+    taken to frequency on the host, must hit the oracle's stored spectrum samples
+    (tests/golden/shear4_bank_64x64.json) to 1e-5; the dual-frame inverse of those
+    coefficients returns the impulse to 1e-5."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "shear4_bank_64x64.json")) as f:
+        g = json.load(f)
+    dims = tuple(g["dims"])
+    b = bank(dims, g["nScales"], tuple(g["shearLevels"]))
+    assert b.R == g["R"]
+    x = np.zeros(dims, dtype=np.float32)
+    x[0, 0] = 1.0
+    C = b.forward(cuda(x))
+    Cn = C.cpu().numpy().astype(np.float64)
+    for j, fl in enumerate(g["filters"]):
+        spec = np.fft.fft2(Cn[j])
+        for k0, k1, v in fl["samples"]:
+            assert abs(spec[k0, k1].real - v) <= 1e-5 and abs(spec[k0, k1].imag) <= 1e-5, (j, k0, k1)
+    y = b.inverse(C).cpu().numpy()
+    assert np.max(np.abs(y - x)) <= 1e-5
