@@ -54,7 +54,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs, objs = [], []
     for src in SOURCES:
         obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
-        extra = ["--split-compile=0"] if src.endswith(".cu") else []
+        # a fixed split count: the device code (and its register allocation) is then the
+        # same whatever the number of host cores of the machine that builds it
+        extra = ["--split-compile=16"] if src.endswith(".cu") else []
         cmd = [nvcc(), *common, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
