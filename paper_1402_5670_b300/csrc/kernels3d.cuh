@@ -222,27 +222,44 @@ __global__ void __launch_bounds__(kPlaneThreads) k_plane(RowArgs p, int nslots) 
       if (next < nitems) load_rows(next, v);  // v is free: in flight during the rest
     }
     __syncthreads();
-    for (int it = tid; it < PAIRS * B; it += kPlaneThreads) {
-      const int kb = it % B, q = it / B;
-      float2 w[A];
+    // Pass 2, and the split of each row pair's spectrum Z = FFT(x0 + i x1) into the two
+    // half rows in registers: the thread of (q, kb) holds Z[kb + B ka], and Z[L2 - k]
+    // sits in the thread of (q, (B - kb) mod B) at index A - 1 - ka (in this thread at
+    // (A - ka) mod A when kb = 0). Whole warps iterate (the B-thread groups never
+    // straddle a warp: B divides 32), so the shuffles see every lane. The half rows go
+    // to P (free: its natural pairs, in RT mode, were read before pass 1).
+    static_assert(32 % B == 0 && (A & (A - 1)) == 0, "partner lanes within a warp");
+    {
+      const int lane = tid & 31;
+      for (int it0 = tid & ~31; it0 < PAIRS * B; it0 += kPlaneThreads) {
+        const int it = it0 + lane;
+        const bool valid = it < PAIRS * B;
+        const int kb = it % B, q = it / B;
+        float2 w[A];
 #pragma unroll
-      for (int a = 0; a < A; ++a) w[a] = W[q * LS + kb * (A + 1) + a];
-      Dft<A, -1>::run(w);
+        for (int a = 0; a < A; ++a)
+          w[a] = valid ? W[q * LS + kb * (A + 1) + a] : make_float2(0.f, 0.f);
+        Dft<A, -1>::run(w);
+        const int partner = (lane & ~(B - 1)) | ((B - kb) & (B - 1));
 #pragma unroll
-      for (int ka = 0; ka < A; ++ka) P[q * L2 + kb + B * ka] = w[ka];
+        for (int ka = 0; ka <= A / 2; ++ka) {
+          const float2 far = w[A - 1 - ka];
+          const float2 oth = make_float2(__shfl_sync(0xffffffffu, far.x, partner),
+                                         __shfl_sync(0xffffffffu, far.y, partner));
+          const float2 wz = kb == 0 ? w[(A - ka) & (A - 1)] : oth;
+          const float2 z = w[ka];
+          if (valid && (ka < A / 2 || kb == 0)) {  // k <= L2 / 2
+            const int k = kb + B * ka;
+            P[(2 * q) * NH + k] = make_float2(0.5f * (z.x + wz.x), 0.5f * (z.y - wz.y));
+            P[(2 * q + 1) * NH + k] = make_float2(0.5f * (z.y + wz.y), 0.5f * (wz.x - z.x));
+          }
+        }
+      }
     }
     __syncthreads();
-    for (int it = tid; it < PAIRS * NH; it += kPlaneThreads) {
-      const int q = it / NH, k = it % NH;
-      const float2 z = P[q * L2 + k];
-      const float2 w = P[q * L2 + ((L2 - k) & (L2 - 1))];
-      W[(2 * q) * NH + k] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
-      W[(2 * q + 1) * NH + k] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
-    }
-    __syncthreads();
-    plane_col_fft<L1, NH, -1>(W, P, W);
+    plane_col_fft<L1, NH, -1>(P, W, P);
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
-    for (int i = tid; i < G::HALF; i += kPlaneThreads) out[p.tm.at(i0, i)] = W[i];
+    for (int i = tid; i < G::HALF; i += kPlaneThreads) out[p.tm.at(i0, i)] = P[i];
     if constexpr (MODE == ROW_RT) {
       __syncthreads();  // P is free once the last axis-1 pass has read it
       if (next < nitems) park(ld);
