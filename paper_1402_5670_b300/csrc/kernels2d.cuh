@@ -801,23 +801,23 @@ __global__ void __launch_bounds__(PAIRS * Split<L>::A, L >= 1024 ? 2 : SL_MINB_R
     }
     float2* out = p.out_half + (int64_t)slot * p.out_stride;
     const int tcs = tm_tc(tm);  // the two rows of a pair sit TC elements apart
-    if constexpr (A == 32) {
+    if constexpr (32 % B == 0 && (A & (A - 1)) == 0 && (PAIRS * B) % 32 == 0) {
       // Split Z = FFT(x0 + i x1) into the half spectra of x0 and x1 in registers: this
       // thread holds Z[k] for k = kb2 + B ka, and Z[L - k] sits in lane (B - kb2) mod B
-      // of its B-lane group at index 31 - ka (or in this thread at (32 - ka) mod 32 when
+      // of its B-lane group at index A - 1 - ka (or in this thread at (A - ka) mod A when
       // kb2 = 0). The in2 threads fill whole warps, so the shuffles are warp-uniform.
       if (in2) {
         const int lane = tid & 31;
         const int partner = (lane & ~(B - 1)) | ((B - kb2) & (B - 1));
         const int row = r0 + 2 * line2;
 #pragma unroll
-        for (int ka = 0; ka <= 16; ++ka) {
-          const float2 far = res[31 - ka];
+        for (int ka = 0; ka <= A / 2; ++ka) {
+          const float2 far = res[A - 1 - ka];
           const float2 oth = make_float2(__shfl_sync(0xffffffffu, far.x, partner),
                                          __shfl_sync(0xffffffffu, far.y, partner));
-          const float2 w = kb2 == 0 ? res[(32 - ka) & 31] : oth;
+          const float2 w = kb2 == 0 ? res[(A - ka) & (A - 1)] : oth;
           const float2 z = res[ka];
-          if (ka < 16 || kb2 == 0) {  // k <= H
+          if (ka < A / 2 || kb2 == 0) {  // k <= H
             float2* o = out + tm.at(row, kb2 + B * ka);
             o[0] = make_float2(0.5f * (z.x + w.x), 0.5f * (z.y - w.y));
             o[tcs] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
